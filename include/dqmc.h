@@ -1,0 +1,212 @@
+/*
+ * dqmc.h -- C ABI of the GB300 kagome DQMC time-slice sweep.
+ *
+ * Method: finite-temperature determinant QMC for the attractive Hubbard model
+ * (Eq. 1 of arXiv 2608.03894, U < 0 is attraction) on an L x L-cell kagome
+ * torus with N = 3 L^2 sites. The hot path per imaginary-time slice is
+ *   (1) the kinetic propagator products e^{-dtau K} G and G e^{+dtau K}, done
+ *       as 2D FFTs over cells per sublattice, a per-momentum 3x3 block multiply
+ *       and inverse FFTs (Sec. II, Eq. 2-6);
+ *   (2) the diagonal e^{V(s)} scaling of the Ising Hubbard-Stratonovich field;
+ *   (3) the Metropolis sweep over the slice with delayed updates: k rank-one
+ *       Sherman-Morrison corrections accumulated and flushed as one rank-k
+ *       product (the delayed-update scheme the paper combines with its FFT
+ *       propagation, Sec. II last paragraph and Sec. III);
+ *   (4) periodic FP64 UDV (QR) stabilisation and recomputation of G.
+ *
+ * Conventions (all calls):
+ *   - Site index i = (x1*L + x2)*3 + a, a in {A,B,C} (Kronecker order of Eq. 3).
+ *   - G_ij = <c_i c_j^+> of one spin species, N x N, ROW-MAJOR, FP64 on the
+ *     host side of this ABI.
+ *   - Ising field s[l-1][i] in {-1,+1}, int8, M x N slice-major, M = beta/dtau.
+ *   - U uses the paper's sign: U <= 0; U > 0 is rejected (DQMC_EINVAL).
+ *   - Interaction in particle-hole symmetric form U (n_up - 1/2)(n_dn - 1/2);
+ *     mu = -1 puts the U = 0 Fermi level at the Dirac point (rho = 2/3).
+ *   - Random numbers: Philox4x32-10, key = seed, counter = (site, slice-1,
+ *     2*sweep + pass, chain | domain << 24); one draw per proposal.
+ *   - Every call returns a dqmc_status; on failure dqmc_last_error() returns a
+ *     thread-local message. No C++ exception crosses this boundary.
+ *   - Host buffers passed in are owned by the caller and only read or written
+ *     during the call. Device memory the library allocates is owned by the
+ *     context and freed by dqmc_destroy.
+ *   - After DQMC_ECUDA or DQMC_ETIMEOUT a context is poisoned: every later
+ *     call except dqmc_destroy returns DQMC_ESTATE.
+ */
+#ifndef DQMC_GB300_H
+#define DQMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dqmc_ctx dqmc_ctx;
+
+typedef enum {
+  DQMC_OK = 0,
+  DQMC_EINVAL = 1,    /* bad argument (size, sign of U, unsupported L, null pointer) */
+  DQMC_ENOMEM = 2,    /* device or host allocation failed */
+  DQMC_ECUDA = 3,     /* a CUDA runtime call or kernel failed */
+  DQMC_ENUMERIC = 4,  /* non-positive or non-finite acceptance ratio, drift above the hard limit */
+  DQMC_ETIMEOUT = 5,  /* a bounded device wait gave up */
+  DQMC_ESTATE = 6     /* context poisoned by an earlier failure, or call out of order */
+} dqmc_status;
+
+/* Binned means and errors of the equal-time estimators (Sec. III and IV):
+ *   S_pair_G  = S_Pair(Gamma), S_pair_dk = S_Pair(Gamma + dk), dk = b1/L,
+ *     symmetric definition (1/N) sum_ij e^{iQ(r_i - r_j)} <D_i^+ D_j + D_j D_i^+>;
+ *   phi2_G, phi2_K = <phi^+ phi>(Q) of the CDW field
+ *     phi(Q) = (1/N) sum_cells e^{iQR}(n_A + w n_B + w^2 n_C), w = e^{2 pi i/3};
+ *     phi2_K is NaN when 3 does not divide L (no K point on the mesh);
+ *   density = (2/N) sum_x (1 - G_xx), ekin = (2/N) sum_ij K_ij (delta_ij - G_ji).
+ * Derived with a jackknife over bins: R_pair = 1 - S(Gamma+dk)/S(Gamma),
+ * P = sqrt(S(Gamma)/N), D_G = sqrt(phi2_G), D_K = sqrt(phi2_K). */
+typedef struct {
+  double S_pair_G, S_pair_dk, phi2_G, phi2_K, density, ekin; /* means */
+  double err[6];                                             /* standard errors over bins */
+  long n_samples;                                            /* measurements accumulated */
+  long n_bins;
+  double R_pair, R_pair_err, P, P_err, D_G, D_K;
+} dqmc_obs;
+
+/* Run statistics. */
+typedef struct {
+  long sweeps;           /* sweeps done since create/load */
+  long proposed;         /* Metropolis proposals (2 N M per sweep) */
+  long accepted;
+  double max_drift;      /* max |G_wrapped - G_fresh| at stabilisation points */
+  double last_drift;     /* same, over the last sweep only */
+  double ms_wrap, ms_update, ms_stab, ms_measure; /* device time per phase (when timing is on) */
+} dqmc_stats;
+
+/* ------------------------------------------------------------------ context API */
+
+/* Validate parameters and create a context for one Markov chain on the current
+ * CUDA device. L >= 1 from the supported set {1,2,3,4,6,8,12,16,24,36}; beta/dtau
+ * a positive integer (1e-9); U <= 0. Device memory is allocated lazily on the
+ * first call that needs it, so dqmc_set_option / dqmc_set_stream /
+ * dqmc_set_allocator / dqmc_set_field may follow. Initial field: Philox
+ * (domain 1), s = +1 iff the low bit of word 0 is set. Returns DQMC_EINVAL on a
+ * bad argument. */
+dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, uint64_t seed,
+                        dqmc_ctx **out);
+
+/* Options (numbers): "k" delay rank (1..64, default 32), "n_stab" slices between
+ * UDV refreshes (default 10), "precision" (0 = plain FP64, 1 = FP32 propagation
+ * and flush with FP64 stabilisation and ratios), "chain" (Philox chain id),
+ * "timing" (1 = per-phase CUDA-event timers), "site_offsets" (1 = S_Pair phases
+ * use site positions R + tau_a, 0 = cell positions), "bin" (measurements per
+ * bin, default 10), "drift_limit" (hard limit, default 1e-3 -> DQMC_ENUMERIC).
+ * "k", "n_stab", "precision" and "chain" are accepted only before the first
+ * sweep; later they return DQMC_ESTATE. */
+dqmc_status dqmc_set_option(dqmc_ctx *ctx, const char *key, double value);
+
+/* Launch every kernel of this context on the given cudaStream_t (e.g. the
+ * current PyTorch stream). NULL = the legacy default stream. */
+dqmc_status dqmc_set_stream(dqmc_ctx *ctx, void *cuda_stream);
+
+/* Route device allocations through the caller (e.g. PyTorch's caching
+ * allocator). alloc(bytes, user) returns a device pointer or NULL; release(ptr,
+ * user) frees it. Must be called before the first allocation (DQMC_ESTATE
+ * otherwise). */
+dqmc_status dqmc_set_allocator(dqmc_ctx *ctx, void *(*alloc)(size_t, void *),
+                               void (*release)(void *, void *), void *user);
+
+/* n_sweeps sweeps: an up pass l = 1..M (wrap, then propose all N sites of slice
+ * l in index order) and a down pass l = M..1 (propose, then unwrap); G is
+ * recomputed from the UDV stacks every n_stab slices. measure != 0 accumulates
+ * the estimators at every up-pass stabilisation point (fresh FP64 G). The call
+ * returns when the work is done (it synchronises the stream). */
+dqmc_status dqmc_sweep(dqmc_ctx *ctx, int n_sweeps, int measure);
+
+/* G(tau_slice), 0 <= slice <= M, recomputed from scratch in FP64 from the
+ * current field (QR chain over all slices; does not touch the running state).
+ * G_out: host, N*N doubles, row-major, caller-owned. */
+dqmc_status dqmc_green(dqmc_ctx *ctx, int slice, double *G_out);
+
+/* The running (wrapped/updated) G at the current slice, converted to FP64.
+ * G_out: host N*N doubles; *slice receives the current slice index. */
+dqmc_status dqmc_get_running_green(dqmc_ctx *ctx, double *G_out, int *slice);
+
+/* Binned means/errors accumulated so far (see dqmc_obs). */
+dqmc_status dqmc_measure(dqmc_ctx *ctx, dqmc_obs *out);
+
+/* Statistics (see dqmc_stats). */
+dqmc_status dqmc_get_stats(dqmc_ctx *ctx, dqmc_stats *out);
+
+/* Copy the field out (M*N int8) or in. Setting the field rebuilds the stacks
+ * and G at tau = 0 (values other than +-1 -> DQMC_EINVAL). */
+dqmc_status dqmc_get_field(dqmc_ctx *ctx, int8_t *s_out);
+dqmc_status dqmc_set_field(dqmc_ctx *ctx, const int8_t *s);
+
+/* Checkpoint: parameters, options, field, sweep counter, statistics and bins.
+ * G is recomputed on load. Binary file; DQMC_EINVAL if the file does not match
+ * the context's (L, beta, dtau, U, mu). */
+dqmc_status dqmc_save(dqmc_ctx *ctx, const char *path);
+dqmc_status dqmc_load(dqmc_ctx *ctx, const char *path);
+
+const char *dqmc_last_error(void);
+void dqmc_destroy(dqmc_ctx *ctx);
+
+/* Library version string. */
+const char *dqmc_version(void);
+
+/* ------------------------------------------------------------------ operator API
+ * Stateless steps of the hot path on caller-owned DEVICE memory, launched on
+ * the given stream (NULL = legacy default stream). They validate sizes and
+ * pointers, return DQMC_EINVAL on misuse, and report launch failures as
+ * DQMC_ECUDA. They are what the parity tests call one step at a time. */
+
+/* Eq. 5-6: kinetic propagator product with fused diagonal scalings.
+ *   side 0 (left, acts on the N-long columns of X):
+ *     Y = diag(post) e^{scale K} diag(pre) X diag(vscale)
+ *   side 1 (right, acts on the N-long rows of X):
+ *     Y = diag(vscale) X diag(pre) e^{scale K} diag(post)
+ * X, Y: N x nvec (side 0) or nvec x N (side 1) row-major with leading dimension
+ * ld >= (side 0 ? nvec : N); Y may alias X. pre/post: length N or NULL;
+ * vscale: length nvec or NULL. _f64: double data and vectors, _f32: float. The
+ * 3x3 momentum blocks e^{scale H(k)} are built on the host in FP64 (cached per
+ * (L, scale)). */
+dqmc_status dqmc_op_propagate_f64(int L, double scale, int side, const double *X, double *Y,
+                                  int nvec, int ld, const double *pre, const double *post,
+                                  const double *vscale, void *stream);
+dqmc_status dqmc_op_propagate_f32(int L, double scale, int side, const float *X, float *Y,
+                                  int nvec, int ld, const float *pre, const float *post,
+                                  const float *vscale, void *stream);
+
+/* Delayed-update block (one CTA, FP64 bookkeeping): propose the kb <= 64 sites
+ * S = [site0, site0+kb) of slice `slice1` (1-based) in order, given
+ * g = G[S,S] (kb x kb, row-major, ld_g), the field row s (N int8, flipped in
+ * place on accept), lambda, the Philox key/counter words. Writes Gamma (kb x kb,
+ * row-major FP64) such that the accepted flips give
+ *   G' = G - G[:,S] Gamma (I - G)[S,:]   (Woodbury form of the sequential
+ *   Sherman-Morrison updates), and accept_count[0] (int). Non-positive or
+ * non-finite ratios set *status = 1 and stop. forced != NULL (kb bytes)
+ * replaces the Metropolis decision. */
+dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, int ld_g,
+                                     int8_t *s, double lambda, uint64_t seed, uint32_t chain,
+                                     uint32_t sweep_pass, int slice1, const uint8_t *forced,
+                                     double *Gamma, int *accept_count, int *status, void *stream);
+
+/* Rank-k flush: G <- G - Gcol * Gamma * (E_S - Grow), with Gcol = G[:,S]
+ * (N x kb, ld kb) and Grow = G[S,:] (kb x N, ld N) taken before the update,
+ * E_S the kb x N selector of S = [site0, site0+kb). G: N x N row-major FP64
+ * (ldG = N). Gamma: kb x kb FP64. */
+dqmc_status dqmc_op_flush_f64(int N, int site0, int kb, double *G, const double *Gcol,
+                              const double *Grow, const double *Gamma, void *stream);
+dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *Gcol,
+                              const float *Grow, const double *Gamma, void *stream);
+
+/* Equal-time estimator sums from one FP64 G (N x N row-major, device): writes
+ * out[6] (host) = S_pair_G, S_pair_dk, phi2_G, phi2_K, density, ekin, with the
+ * same definitions and phase conventions as dqmc_obs (site_offsets as the
+ * option). Synchronises the stream. */
+dqmc_status dqmc_op_measure(int L, const double *G, int site_offsets, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQMC_GB300_H */

@@ -1,0 +1,81 @@
+// Shared device/host helpers of the GB300 kagome DQMC library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dqmc.h"
+
+namespace dq {
+
+// ------------------------------------------------------------------ errors
+// Thread-local last-error message behind dqmc_last_error().
+void set_error(const std::string &msg);
+dqmc_status fail(dqmc_status st, const std::string &msg);
+dqmc_status cuda_fail(cudaError_t e, const char *what);
+
+#define DQ_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return ::dq::cuda_fail(_e, #call); \
+  } while (0)
+
+#define DQ_CHECK(st)                   \
+  do {                                 \
+    dqmc_status _s = (st);             \
+    if (_s != DQMC_OK) return _s;      \
+  } while (0)
+
+// ------------------------------------------------------------------ small types
+template <typename T> struct cpx { T x, y; };
+
+template <typename T> __host__ __device__ __forceinline__ cpx<T> mkc(T a, T b) { return cpx<T>{a, b}; }
+
+// Supported torus sizes (one register-resident FFT instantiation each).
+constexpr int kSupportedL[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 36};
+inline bool supported_L(int L) {
+  for (int v : kSupportedL)
+    if (v == L) return true;
+  return false;
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Written from its published definition (Salmon, Moraes, Dror, Shaw, SC'11):
+// two 32x32->64 multiplies per round on words 0 and 2, the high halves mixed
+// with words 1 and 3 and the round key, key bumped by the Weyl constants.
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// u in [0,1) from 53 bits: ((r0 >> 5) 2^26 + (r1 >> 6)) 2^-53.
+__host__ __device__ __forceinline__ double uniform53(uint32_t r0, uint32_t r1) {
+  return ((double)(r0 >> 5) * 67108864.0 + (double)(r1 >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+constexpr uint32_t kDomainMetropolis = 0u;
+constexpr uint32_t kDomainInit = 1u;
+
+// ------------------------------------------------------------------ launch helpers
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace dq

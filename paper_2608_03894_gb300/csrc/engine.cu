@@ -1,0 +1,1030 @@
+// DQMC chain engine and the C ABI of include/dqmc.h.
+//
+// The sweep is a fixed sequence of kernel launches on one stream; the host
+// never waits inside a sweep. Per slice visit (up pass):
+//   wrap   G <- e^{V} e^{-dtau K} G e^{+dtau K} e^{-V}     2 FFT propagator passes
+//   update gather block 0; per block of k sites: Metropolis (1 CTA) + rank-k flush
+//   stab   every n_stab slices: UDV stack update (FFT propagation of the
+//          orthogonal factor in FP64, pre-pivoted Householder QR) and the
+//          scale-separated recomputation of G; drift = max |G - G_fresh|
+// The down pass runs the same steps in reverse order (update, then unwrap).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "lattice_host.h"
+#include "linalg.cuh"
+
+namespace dq {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+dqmc_status fail(dqmc_status st, const std::string &msg) {
+  set_error(msg);
+  return st;
+}
+dqmc_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(DQMC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------- shared-memory opt-in
+// cudaFuncSetAttribute is per device; remember (function, device) pairs.
+static std::mutex g_attr_mu;
+static std::map<std::pair<const void *, int>, int> g_attr;
+cudaError_t ensure_smem_attr(const void *func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  auto key = std::make_pair(func, dev);
+  auto it = g_attr.find(key);
+  if (it != g_attr.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) g_attr[key] = bytes;
+  return e;
+}
+
+// ---------------------------------------------------------------- small kernels
+// e^{V_i} = e^{lambda s_i + dtau mu}: two values, computed on the host
+__global__ void expv_kernel(const int8_t *s, int N, double vp, double vm, double *ev64,
+                            double *evi64, float *ev32, float *evi32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double v = s[i] > 0 ? vp : vm;
+  const double vi = s[i] > 0 ? 1.0 / vp : 1.0 / vm;
+  ev64[i] = v;
+  evi64[i] = vi;
+  ev32[i] = (float)v;
+  evi32[i] = (float)vi;
+}
+
+// initial field from Philox, domain 1: s = +1 iff the low bit of word 0 is set
+__global__ void init_field_kernel(int8_t *s, int M, int N, uint32_t k0, uint32_t k1, uint32_t c3) {
+  const long total = (long)M * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int l = (int)(e / N), i = (int)(e % N);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)l, 0u, c3), k0, k1);
+    s[e] = (r.x & 1u) ? (int8_t)1 : (int8_t)-1;
+  }
+}
+
+// ---------------------------------------------------------------- block table cache
+struct TableKey {
+  int dev, L, prec;
+  uint64_t scale_bits;
+  bool operator<(const TableKey &o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (L != o.L) return L < o.L;
+    if (prec != o.prec) return prec < o.prec;
+    return scale_bits < o.scale_bits;
+  }
+};
+static std::mutex g_tab_mu;
+static std::map<TableKey, void *> g_tables;
+
+// Device table of e^{scale H(k)} / L^2 (half spectrum), FP64 (prec 0) or FP32 (prec 1).
+static dqmc_status get_table(int L, double scale, int prec, const void **out) {
+  int dev = 0;
+  DQ_CUDA(cudaGetDevice(&dev));
+  uint64_t bits;
+  std::memcpy(&bits, &scale, sizeof(bits));
+  TableKey key{dev, L, prec, bits};
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  auto it = g_tables.find(key);
+  if (it != g_tables.end()) {
+    *out = it->second;
+    return DQMC_OK;
+  }
+  std::vector<cd> tab = block_exp_table(L, scale);
+  void *d = nullptr;
+  if (prec == 0) {
+    std::vector<cpx<double>> h(tab.size());
+    for (size_t q = 0; q < tab.size(); ++q) h[q] = cpx<double>{tab[q].real(), tab[q].imag()};
+    DQ_CUDA(cudaMalloc(&d, h.size() * sizeof(cpx<double>)));
+    DQ_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(cpx<double>), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<cpx<float>> h(tab.size());
+    for (size_t q = 0; q < tab.size(); ++q)
+      h[q] = cpx<float>{(float)tab[q].real(), (float)tab[q].imag()};
+    DQ_CUDA(cudaMalloc(&d, h.size() * sizeof(cpx<float>)));
+    DQ_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(cpx<float>), cudaMemcpyHostToDevice));
+  }
+  g_tables[key] = d;
+  *out = d;
+  return DQMC_OK;
+}
+
+}  // namespace dq
+
+using namespace dq;
+
+// ---------------------------------------------------------------- context
+struct UDVd {
+  double *U = nullptr, *D = nullptr, *T = nullptr;
+};
+
+struct dqmc_ctx {
+  // parameters
+  int L = 0, N = 0, M = 0;
+  double beta = 0, dtau = 0, U = 0, mu = 0, thop = 1.0, lam = 0;
+  uint64_t seed = 0;
+  // options
+  int k = 32, n_stab = 10, precision = 0, chain = 0, timing = 0, site_offsets = 1, bin = 10;
+  double drift_limit = 1e-3;
+  // runtime
+  cudaStream_t stream = nullptr;
+  void *(*ualloc)(size_t, void *) = nullptr;
+  void (*ufree)(void *, void *) = nullptr;
+  void *uuser = nullptr;
+  std::vector<void *> allocs;
+  int device = 0;
+  bool allocated = false, ready = false, poisoned = false, started = false;
+  int C = 0;
+  std::vector<int> tau;
+  int cur_slice = 0;
+  // device buffers
+  int8_t *field = nullptr;
+  double *G64 = nullptr;  // working G (fp64 mode) / scratch fp64 copy (mixed)
+  float *G32 = nullptr;   // working G (mixed)
+  double *Gf = nullptr;   // fresh G
+  const cpx<double> *E64m = nullptr, *E64p = nullptr;
+  const cpx<float> *E32m = nullptr, *E32p = nullptr;
+  std::vector<UDVd> right, left;
+  UDVd tmpA, tmpB;                       // scratch UDVs for dqmc_green
+  double *X = nullptr, *Xp = nullptr, *Tp = nullptr, *Dp = nullptr, *norms = nullptr;
+  int *perm = nullptr;
+  double *Mm = nullptr, *Bm = nullptr, *Z = nullptr;
+  double *drmax_inv = nullptr, *drmin = nullptr, *dlmax_inv = nullptr, *dlmin = nullptr;
+  QRWork qr;
+  double *ev64 = nullptr, *evi64 = nullptr;
+  float *ev32 = nullptr, *evi32 = nullptr;
+  void *Gcol[2] = {nullptr, nullptr}, *Grow[2] = {nullptr, nullptr};
+  double *Gamma = nullptr;
+  int *acc = nullptr, *status = nullptr;
+  unsigned long long *total_acc = nullptr;
+  double *drift = nullptr, *drift_max = nullptr;
+  double *meas_raw = nullptr, *meas_obs = nullptr;  // obs: capacity meas_cap x 6
+  int meas_cap = 0, meas_n = 0;
+  double *ph_pc = nullptr, *ph_ps = nullptr, *ph_wgc = nullptr, *ph_wgs = nullptr,
+         *ph_wkc = nullptr, *ph_wks = nullptr;
+  int *nbr = nullptr;
+  bool haveK = false;
+  // host statistics
+  long sweeps = 0, proposed = 0, accepted = 0;
+  double max_drift = 0.0, last_drift = 0.0;
+  std::vector<std::array<double, 6>> samples;
+  double ms_wrap = 0, ms_update = 0, ms_stab = 0, ms_measure = 0;
+};
+
+namespace {
+
+dqmc_status ctx_alloc(dqmc_ctx *c, void **p, size_t bytes) {
+  void *q = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->ualloc) {
+    q = c->ualloc(bytes, c->uuser);
+    if (!q) return fail(DQMC_ENOMEM, "allocator callback returned NULL");
+  } else {
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return fail(DQMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  *p = q;
+  return DQMC_OK;
+}
+template <typename T> dqmc_status ctx_alloc_n(dqmc_ctx *c, T **p, size_t n) {
+  void *q = nullptr;
+  DQ_CHECK(ctx_alloc(c, &q, n * sizeof(T)));
+  *p = static_cast<T *>(q);
+  return DQMC_OK;
+}
+
+dqmc_status poison(dqmc_ctx *c, dqmc_status st) {
+  if (st == DQMC_ECUDA || st == DQMC_ETIMEOUT) c->poisoned = true;
+  return st;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return poison(c, cuda_fail(_e, #call)); \
+  } while (0)
+
+bool valid_k(int k) { return k == 4 || k == 8 || k == 16 || k == 32 || k == 64; }
+
+// ---------------------------------------------------------------- allocation
+dqmc_status ensure_alloc(dqmc_ctx *c) {
+  if (c->allocated) return DQMC_OK;
+  CK(cudaGetDevice(&c->device));
+  const int N = c->N, M = c->M;
+  const size_t NN = (size_t)N * N;
+  c->C = (M + c->n_stab - 1) / c->n_stab;
+  c->tau.resize(c->C + 1);
+  for (int q = 0; q <= c->C; ++q) c->tau[q] = std::min(q * c->n_stab, M);
+
+  DQ_CHECK(ctx_alloc_n(c, &c->field, (size_t)M * N));
+  DQ_CHECK(ctx_alloc_n(c, &c->G64, NN));
+  DQ_CHECK(ctx_alloc_n(c, &c->Gf, NN));
+  if (c->precision == 1) DQ_CHECK(ctx_alloc_n(c, &c->G32, NN));
+  c->right.resize(c->C + 1);
+  c->left.resize(c->C + 1);
+  for (int q = 0; q <= c->C; ++q) {
+    for (UDVd *u : {&c->right[q], &c->left[q]}) {
+      DQ_CHECK(ctx_alloc_n(c, &u->U, NN));
+      DQ_CHECK(ctx_alloc_n(c, &u->T, NN));
+      DQ_CHECK(ctx_alloc_n(c, &u->D, (size_t)N));
+    }
+  }
+  for (UDVd *u : {&c->tmpA, &c->tmpB}) {
+    DQ_CHECK(ctx_alloc_n(c, &u->U, NN));
+    DQ_CHECK(ctx_alloc_n(c, &u->T, NN));
+    DQ_CHECK(ctx_alloc_n(c, &u->D, (size_t)N));
+  }
+  DQ_CHECK(ctx_alloc_n(c, &c->X, NN));
+  DQ_CHECK(ctx_alloc_n(c, &c->Xp, NN));
+  DQ_CHECK(ctx_alloc_n(c, &c->Tp, NN));
+  DQ_CHECK(ctx_alloc_n(c, &c->Dp, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->norms, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->perm, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->Mm, NN));
+  DQ_CHECK(ctx_alloc_n(c, &c->Bm, NN));
+  DQ_CHECK(ctx_alloc_n(c, &c->Z, NN));
+  DQ_CHECK(ctx_alloc_n(c, &c->drmax_inv, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->drmin, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->dlmax_inv, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->dlmin, (size_t)N));
+  double *qrmem = nullptr;
+  DQ_CHECK(ctx_alloc_n(c, &qrmem, qr_work_doubles(N)));
+  qr_work_bind(c->qr, N, qrmem);
+  CK(cudaMemsetAsync(qrmem, 0, qr_work_doubles(N) * sizeof(double), c->stream));
+  DQ_CHECK(ctx_alloc_n(c, &c->ev64, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->evi64, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->ev32, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->evi32, (size_t)N));
+  const size_t es = c->precision == 1 ? sizeof(float) : sizeof(double);
+  for (int b = 0; b < 2; ++b) {
+    DQ_CHECK(ctx_alloc(c, &c->Gcol[b], (size_t)N * c->k * es));
+    DQ_CHECK(ctx_alloc(c, &c->Grow[b], (size_t)N * c->k * es));
+    CK(cudaMemsetAsync(c->Gcol[b], 0, (size_t)N * c->k * es, c->stream));
+    CK(cudaMemsetAsync(c->Grow[b], 0, (size_t)N * c->k * es, c->stream));
+  }
+  DQ_CHECK(ctx_alloc_n(c, &c->Gamma, (size_t)c->k * c->k));
+  DQ_CHECK(ctx_alloc_n(c, &c->acc, 4));
+  DQ_CHECK(ctx_alloc_n(c, &c->status, 4));
+  DQ_CHECK(ctx_alloc_n(c, &c->total_acc, 1));
+  DQ_CHECK(ctx_alloc_n(c, &c->drift, 1));
+  DQ_CHECK(ctx_alloc_n(c, &c->drift_max, 1));
+  DQ_CHECK(ctx_alloc_n(c, &c->meas_raw, 16));
+  CK(cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->stream));
+  CK(cudaMemsetAsync(c->total_acc, 0, sizeof(unsigned long long), c->stream));
+  CK(cudaMemsetAsync(c->drift_max, 0, sizeof(double), c->stream));
+
+  // tables
+  const void *t = nullptr;
+  DQ_CHECK(get_table(c->L, -c->dtau, 0, &t));
+  c->E64m = static_cast<const cpx<double> *>(t);
+  DQ_CHECK(get_table(c->L, c->dtau, 0, &t));
+  c->E64p = static_cast<const cpx<double> *>(t);
+  DQ_CHECK(get_table(c->L, -c->dtau, 1, &t));
+  c->E32m = static_cast<const cpx<float> *>(t);
+  DQ_CHECK(get_table(c->L, c->dtau, 1, &t));
+  c->E32p = static_cast<const cpx<float> *>(t);
+
+  // measurement phases
+  const int L = c->L;
+  std::vector<double> pc(N), ps(N), wgc(N), wgs(N), wkc(N), wks(N);
+  std::vector<int> nb(4 * (size_t)N);
+  const double two_pi = 6.283185307179586476925286766559;
+  const double fA[3][2] = {{0.0, 0.0}, {0.0, -0.5}, {-0.5, 0.0}};  // tau_a in units of a1, a2
+  c->haveK = (L % 3 == 0);
+  const int km1 = L / 3, km2 = 2 * L / 3;  // Dirac point K where the dispersive bands touch
+  std::vector<int> fill(N, 0);
+  for (int x1 = 0; x1 < L; ++x1)
+    for (int x2 = 0; x2 < L; ++x2)
+      for (int a = 0; a < 3; ++a) {
+        const int i = (x1 * L + x2) * 3 + a;
+        double f1 = x1, f2 = x2;
+        if (c->site_offsets) {
+          f1 += fA[a][0];
+          f2 += fA[a][1];
+        }
+        const double th = two_pi * ((double)(1 % L) * f1 / L);  // Gamma + dk = (1, 0)
+        pc[i] = std::cos(th);
+        ps[i] = std::sin(th);
+        const double pa = two_pi * a / 3.0;
+        wgc[i] = std::cos(pa);
+        wgs[i] = std::sin(pa);
+        const double pk = two_pi * ((double)((km1 * x1 + km2 * x2) % std::max(L, 1)) / L) + pa;
+        wkc[i] = std::cos(pk);
+        wks[i] = std::sin(pk);
+      }
+  for (const Bond &bd : kKagomeBonds) {
+    for (int x1 = 0; x1 < L; ++x1)
+      for (int x2 = 0; x2 < L; ++x2) {
+        const int i = (x1 * L + x2) * 3 + bd.a;
+        const int y1 = ((x1 + bd.d1) % L + L) % L, y2 = ((x2 + bd.d2) % L + L) % L;
+        const int j = (y1 * L + y2) * 3 + bd.b;
+        nb[4 * (size_t)i + fill[i]++] = j;
+        nb[4 * (size_t)j + fill[j]++] = i;
+      }
+  }
+  DQ_CHECK(ctx_alloc_n(c, &c->ph_pc, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->ph_ps, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->ph_wgc, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->ph_wgs, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->ph_wkc, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->ph_wks, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->nbr, 4 * (size_t)N));
+  CK(cudaMemcpyAsync(c->ph_pc, pc.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->ph_ps, ps.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->ph_wgc, wgc.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->ph_wgs, wgs.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->ph_wkc, wkc.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->ph_wks, wks.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->nbr, nb.data(), 4 * (size_t)N * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+
+  // initial field
+  const uint32_t k0 = (uint32_t)(c->seed & 0xffffffffu), k1 = (uint32_t)(c->seed >> 32);
+  const uint32_t c3 = ((uint32_t)c->chain & 0xffffffu) | (kDomainInit << 24);
+  init_field_kernel<<<256, 256, 0, c->stream>>>(c->field, M, N, k0, k1, c3);
+  CK(cudaGetLastError());
+  c->allocated = true;
+  return DQMC_OK;
+}
+
+// ---------------------------------------------------------------- propagation helpers
+dqmc_status compute_expv(dqmc_ctx *c, int l) {
+  const double vp = std::exp(c->lam + c->dtau * c->mu), vm = std::exp(-c->lam + c->dtau * c->mu);
+  expv_kernel<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->field + (size_t)(l - 1) * c->N, c->N,
+                                                         vp, vm, c->ev64, c->evi64, c->ev32,
+                                                         c->evi32);
+  CK(cudaGetLastError());
+  return DQMC_OK;
+}
+
+// G <- e^{V} e^{-dtau K} G e^{+dtau K} e^{-V}
+dqmc_status wrap(dqmc_ctx *c, int l) {
+  DQ_CHECK(compute_expv(c, l));
+  const int N = c->N;
+  if (c->precision == 0) {
+    CK(launch_prop_f64(c->L, 0, c->G64, c->G64, N, N, c->E64m, nullptr, nullptr, nullptr, c->stream));
+    CK(launch_prop_f64(c->L, 1, c->G64, c->G64, N, N, c->E64p, nullptr, c->evi64, c->ev64, c->stream));
+  } else {
+    CK(launch_prop_f32(c->L, 0, c->G32, c->G32, N, N, c->E32m, nullptr, nullptr, nullptr, c->stream));
+    CK(launch_prop_f32(c->L, 1, c->G32, c->G32, N, N, c->E32p, nullptr, c->evi32, c->ev32, c->stream));
+  }
+  return DQMC_OK;
+}
+
+// G <- e^{+dtau K} e^{-V} G e^{V} e^{-dtau K}
+dqmc_status unwrap(dqmc_ctx *c, int l) {
+  DQ_CHECK(compute_expv(c, l));
+  const int N = c->N;
+  if (c->precision == 0) {
+    CK(launch_prop_f64(c->L, 0, c->G64, c->G64, N, N, c->E64p, c->evi64, nullptr, c->ev64, c->stream));
+    CK(launch_prop_f64(c->L, 1, c->G64, c->G64, N, N, c->E64m, nullptr, nullptr, nullptr, c->stream));
+  } else {
+    CK(launch_prop_f32(c->L, 0, c->G32, c->G32, N, N, c->E32p, c->evi32, nullptr, c->ev32, c->stream));
+    CK(launch_prop_f32(c->L, 1, c->G32, c->G32, N, N, c->E32m, nullptr, nullptr, nullptr, c->stream));
+  }
+  return DQMC_OK;
+}
+
+// ---------------------------------------------------------------- delayed update of one slice
+template <typename T>
+dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
+  const int N = c->N, K = c->k;
+  const int nblk = (N + K - 1) / K;
+  T *Gc[2] = {static_cast<T *>(c->Gcol[0]), static_cast<T *>(c->Gcol[1])};
+  T *Gr[2] = {static_cast<T *>(c->Grow[0]), static_cast<T *>(c->Grow[1])};
+  CK(launch_gather<T>(N, 0, std::min(K, N), K, G, Gc[0], Gr[0], c->stream));
+  MetroArgs ma;
+  ma.N = N;
+  ma.K = K;
+  ma.ld_g = N;
+  ma.e2l = std::exp(2.0 * c->lam);
+  ma.em2l = std::exp(-2.0 * c->lam);
+  ma.k0 = (uint32_t)(c->seed & 0xffffffffu);
+  ma.k1 = (uint32_t)(c->seed >> 32);
+  ma.c2 = (uint32_t)(2 * c->sweeps + pas);
+  ma.c3 = ((uint32_t)c->chain & 0xffffffu) | (kDomainMetropolis << 24);
+  ma.slice0 = l - 1;
+  int8_t *s = c->field + (size_t)(l - 1) * N;
+  for (int b = 0; b < nblk; ++b) {
+    const int s0 = b * K, kb = std::min(K, N - s0);
+    ma.s0 = s0;
+    ma.kb = kb;
+    CK(launch_metropolis<T>(ma, Gr[b & 1] + s0, s, nullptr, c->Gamma, c->acc, c->status,
+                            c->total_acc, c->stream));
+    FlushArgs fa;
+    fa.N = N;
+    fa.s0 = s0;
+    fa.kb = kb;
+    fa.ns0 = (b + 1 < nblk) ? s0 + K : 0;
+    fa.nkb = (b + 1 < nblk) ? std::min(K, N - s0 - K) : 0;
+    fa.rows_per_cta = 0;
+    CK(launch_flush<T>(K, fa, G, Gc[b & 1], Gr[b & 1], c->Gamma, c->acc, Gc[(b + 1) & 1],
+                       Gr[(b + 1) & 1], c->stream));
+  }
+  c->proposed += N;
+  return DQMC_OK;
+}
+
+dqmc_status update_slice(dqmc_ctx *c, int l, int pas) {
+  return c->precision == 0 ? update_slice_t<double>(c, c->G64, l, pas)
+                           : update_slice_t<float>(c, c->G32, l, pas);
+}
+
+// ---------------------------------------------------------------- UDV stacks (FP64)
+// dst = (chunk) src, chunk = B_{l1} ... B_{l0} (right, l0 < l1) applied as
+// X <- e^{V} e^{-dtau K} X, or B_{l0}^T ... B_{l1}^T (transposed left form)
+// applied as X <- e^{-dtau K} e^{V} X, slices visited in the given order.
+dqmc_status udv_advance(dqmc_ctx *c, const UDVd &src, UDVd &dst, const std::vector<int> &slices,
+                        bool transposed) {
+  const int N = c->N;
+  const size_t NN = (size_t)N * N;
+  CK(cudaMemcpyAsync(c->X, src.U, NN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  for (int l : slices) {
+    DQ_CHECK(compute_expv(c, l));
+    if (!transposed)
+      CK(launch_prop_f64(c->L, 0, c->X, c->X, N, N, c->E64m, nullptr, c->ev64, nullptr, c->stream));
+    else
+      CK(launch_prop_f64(c->L, 0, c->X, c->X, N, N, c->E64m, c->ev64, nullptr, nullptr, c->stream));
+  }
+  // pre-pivoting: columns ordered by ||X_j|| D_j, descending
+  CK(column_norms_scaled(c->X, N, src.D, c->norms, c->stream));
+  CK(argsort_desc(c->norms, N, c->perm, c->stream));
+  CK(permute_udv(c->X, src.D, src.T, c->perm, N, c->Xp, c->Dp, c->Tp, c->stream));
+  CK(qr_factor(c->Xp, N, c->qr, c->stream));
+  CK(qr_form_q(dst.U, N, c->qr, c->stream));
+  CK(udv_diag_and_scale(c->Xp, N, c->Dp, dst.D, c->stream));
+  // T_new = R'' (P^T T_old)
+  CK(dgemm(false, false, N, N, N, 1.0, c->Xp, N, c->Tp, N, 0.0, dst.T, N, nullptr, nullptr, c->stream));
+  return DQMC_OK;
+}
+
+dqmc_status udv_identity(dqmc_ctx *c, UDVd &u) {
+  CK(set_identity(u.U, c->N, c->N, c->stream));
+  CK(set_identity(u.T, c->N, c->N, c->stream));
+  CK(set_value(u.D, c->N, 1.0, c->stream));
+  return DQMC_OK;
+}
+
+// G_fresh = (I + B(tau,0) B(beta,tau))^{-1} from right = B(tau,0) = U_r D_r T_r and
+// left = B(beta,tau)^T = U' D_l T' by the scale-separated inversion:
+//   G = U' Dlmax^{-1} [Drmax^{-1} U_r^T U' Dlmax^{-1} + Drmin T_r T'^T Dlmin]^{-1} Drmax^{-1} U_r^T
+dqmc_status combine(dqmc_ctx *c, const UDVd &r, const UDVd &lf, double *Gout) {
+  const int N = c->N;
+  CK(split_scales(r.D, N, c->drmax_inv, c->drmin, c->stream));
+  CK(split_scales(lf.D, N, c->dlmax_inv, c->dlmin, c->stream));
+  CK(dgemm(true, false, N, N, N, 1.0, r.U, N, lf.U, N, 0.0, c->Mm, N, c->drmax_inv, c->dlmax_inv, c->stream));
+  CK(dgemm(false, true, N, N, N, 1.0, r.T, N, lf.T, N, 1.0, c->Mm, N, c->drmin, c->dlmin, c->stream));
+  CK(transpose_scale(r.U, N, c->Bm, N, c->drmax_inv, c->stream));
+  CK(qr_factor(c->Mm, N, c->qr, c->stream));
+  CK(qr_apply_qt(c->Bm, N, N, N, c->qr, c->stream));
+  CK(qr_solve_r(c->Mm, N, c->Bm, c->Z, N, c->qr, c->stream));
+  CK(scale_rows_cols(c->Z, N, N, c->dlmax_inv, nullptr, c->stream));
+  CK(dgemm(false, false, N, N, N, 1.0, lf.U, N, c->Z, N, 0.0, Gout, N, nullptr, nullptr, c->stream));
+  return DQMC_OK;
+}
+
+// replace the running G by G_fresh(stack c), recording the drift
+dqmc_status refresh(dqmc_ctx *c, int q, bool record_drift) {
+  const int N = c->N;
+  DQ_CHECK(combine(c, c->right[q], c->left[q], c->Gf));
+  if (c->precision == 0) {
+    if (record_drift) CK(max_abs_diff_f64(c->Gf, c->G64, N, c->drift, c->stream));
+    CK(cudaMemcpyAsync(c->G64, c->Gf, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    if (record_drift) CK(max_abs_diff_f32(c->Gf, c->G32, N, c->drift, c->stream));
+    CK(convert_f64_to_f32(c->Gf, c->G32, (long)N * N, c->stream));
+  }
+  return DQMC_OK;
+}
+
+__global__ void drift_max_kernel(const double *d, double *mx) {
+  const double v = *d;
+  if (v != v || v > *mx) *mx = v;
+}
+
+dqmc_status ensure_ready(dqmc_ctx *c) {
+  DQ_CHECK(ensure_alloc(c));
+  if (c->ready) return DQMC_OK;
+  DQ_CHECK(udv_identity(c, c->left[c->C]));
+  for (int q = c->C - 1; q >= 0; --q) {
+    std::vector<int> sl;
+    for (int l = c->tau[q + 1]; l > c->tau[q]; --l) sl.push_back(l);
+    DQ_CHECK(udv_advance(c, c->left[q + 1], c->left[q], sl, true));
+  }
+  DQ_CHECK(udv_identity(c, c->right[0]));
+  DQ_CHECK(refresh(c, 0, false));
+  c->cur_slice = 0;
+  c->ready = true;
+  CK(cudaStreamSynchronize(c->stream));
+  return DQMC_OK;
+}
+
+dqmc_status measure_now(dqmc_ctx *c) {
+  if (c->meas_n >= c->meas_cap) {
+    // grow: keep old contents
+    const int cap = std::max(64, 2 * c->meas_cap);
+    double *nb = nullptr;
+    DQ_CHECK(ctx_alloc_n(c, &nb, (size_t)cap * 6));
+    if (c->meas_obs && c->meas_n)
+      CK(cudaMemcpyAsync(nb, c->meas_obs, (size_t)c->meas_n * 6 * sizeof(double),
+                         cudaMemcpyDeviceToDevice, c->stream));
+    c->meas_obs = nb;
+    c->meas_cap = cap;
+  }
+  MeasTables t{c->ph_pc, c->ph_ps, c->ph_wgc, c->ph_wgs, c->haveK ? c->ph_wkc : nullptr,
+               c->haveK ? c->ph_wks : nullptr, c->nbr};
+  CK(launch_measure(c->Gf, c->N, t, c->meas_raw, c->thop, c->meas_obs + (size_t)c->meas_n * 6, c->stream));
+  c->meas_n++;
+  return DQMC_OK;
+}
+
+struct PhaseTimer {
+  dqmc_ctx *c;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+  explicit PhaseTimer(dqmc_ctx *cc) : c(cc) {}
+  void start(int ph, cudaEvent_t *e) {
+    if (!c->timing) return;
+    cudaEventCreate(e);
+    cudaEventRecord(*e, c->stream);
+    (void)ph;
+  }
+  void stop(int ph, cudaEvent_t s) {
+    if (!c->timing) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, c->stream);
+    ev[ph].push_back({s, e});
+  }
+  void collect() {
+    double *acc[4] = {&c->ms_wrap, &c->ms_update, &c->ms_stab, &c->ms_measure};
+    for (int ph = 0; ph < 4; ++ph) {
+      for (auto &p : ev[ph]) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.first, p.second);
+        *acc[ph] += ms;
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+      }
+      ev[ph].clear();
+    }
+  }
+};
+
+dqmc_status one_sweep(dqmc_ctx *c, bool measure, PhaseTimer &tm) {
+  int q = 1;
+  cudaEvent_t e0 = nullptr;
+  for (int l = 1; l <= c->M; ++l) {
+    tm.start(0, &e0);
+    DQ_CHECK(wrap(c, l));
+    tm.stop(0, e0);
+    tm.start(1, &e0);
+    DQ_CHECK(update_slice(c, l, 0));
+    tm.stop(1, e0);
+    c->cur_slice = l;
+    if (l == c->tau[q]) {
+      tm.start(2, &e0);
+      std::vector<int> sl;
+      for (int m = c->tau[q - 1] + 1; m <= c->tau[q]; ++m) sl.push_back(m);
+      DQ_CHECK(udv_advance(c, c->right[q - 1], c->right[q], sl, false));
+      DQ_CHECK(refresh(c, q, true));
+      drift_max_kernel<<<1, 1, 0, c->stream>>>(c->drift, c->drift_max);
+      tm.stop(2, e0);
+      if (measure) {
+        tm.start(3, &e0);
+        DQ_CHECK(measure_now(c));
+        tm.stop(3, e0);
+      }
+      ++q;
+    }
+  }
+  q = c->C - 1;
+  for (int l = c->M; l >= 1; --l) {
+    tm.start(1, &e0);
+    DQ_CHECK(update_slice(c, l, 1));
+    tm.stop(1, e0);
+    tm.start(0, &e0);
+    DQ_CHECK(unwrap(c, l));
+    tm.stop(0, e0);
+    c->cur_slice = l - 1;
+    if (q >= 0 && l - 1 == c->tau[q]) {
+      tm.start(2, &e0);
+      std::vector<int> sl;
+      for (int m = c->tau[q + 1]; m > c->tau[q]; --m) sl.push_back(m);
+      DQ_CHECK(udv_advance(c, c->left[q + 1], c->left[q], sl, true));
+      DQ_CHECK(refresh(c, q, true));
+      drift_max_kernel<<<1, 1, 0, c->stream>>>(c->drift, c->drift_max);
+      tm.stop(2, e0);
+      --q;
+    }
+  }
+  c->sweeps++;
+  return DQMC_OK;
+}
+
+dqmc_status check_ctx(dqmc_ctx *c) {
+  if (!c) return fail(DQMC_EINVAL, "null context");
+  if (c->poisoned) return fail(DQMC_ESTATE, "context is unusable after an earlier CUDA failure");
+  return DQMC_OK;
+}
+
+dqmc_status read_status(dqmc_ctx *c) {
+  int st[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  unsigned long long tot = 0;
+  CK(cudaMemcpyAsync(&tot, c->total_acc, sizeof(tot), cudaMemcpyDeviceToHost, c->stream));
+  double dm = 0.0;
+  CK(cudaMemcpyAsync(&dm, c->drift_max, sizeof(dm), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->accepted = (long)tot;
+  c->last_drift = dm;
+  c->max_drift = std::max(c->max_drift, dm);
+  if (st[0] != 0) return fail(DQMC_ENUMERIC, "non-positive or non-finite acceptance ratio");
+  if (!(dm <= c->drift_limit)) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "stabilisation drift %.3e above the limit %.3e", dm, c->drift_limit);
+    return fail(DQMC_ENUMERIC, buf);
+  }
+  return DQMC_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *dqmc_version(void) { return "dqmc-gb300 0.1 (sm_103a)"; }
+
+const char *dqmc_last_error(void) { return g_last_error.c_str(); }
+
+dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, uint64_t seed,
+                        dqmc_ctx **out) {
+  if (!out) return fail(DQMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!supported_L(L)) return fail(DQMC_EINVAL, "unsupported L (supported: 1,2,3,4,6,8,12,16,24,36)");
+  if (!(dtau > 0.0) || !(beta > 0.0)) return fail(DQMC_EINVAL, "beta and dtau must be positive");
+  const double Mr = beta / dtau;
+  if (std::fabs(Mr - std::round(Mr)) > 1e-9 || std::round(Mr) < 1)
+    return fail(DQMC_EINVAL, "beta / dtau must be a positive integer");
+  if (!(U <= 0.0)) return fail(DQMC_EINVAL, "U must be <= 0 (attractive, paper's sign)");
+  if (!std::isfinite(mu)) return fail(DQMC_EINVAL, "mu must be finite");
+  dqmc_ctx *c = new (std::nothrow) dqmc_ctx();
+  if (!c) return fail(DQMC_ENOMEM, "host allocation failed");
+  c->L = L;
+  c->N = 3 * L * L;
+  c->M = (int)std::lround(Mr);
+  c->beta = beta;
+  c->dtau = dtau;
+  c->U = U;
+  c->mu = mu;
+  c->seed = seed;
+  c->lam = std::acosh(std::exp(dtau * std::fabs(U) / 2.0));
+  if (c->N < c->k) c->k = 4;
+  *out = c;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) {
+  DQ_CHECK(check_ctx(c));
+  if (!key) return fail(DQMC_EINVAL, "key is NULL");
+  const std::string k(key);
+  const bool fixed = (k == "k" || k == "n_stab" || k == "precision" || k == "chain");
+  if (fixed && c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
+  if (k == "k") {
+    if (!valid_k((int)v) || (double)(int)v != v) return fail(DQMC_EINVAL, "k must be one of 4, 8, 16, 32, 64");
+    c->k = (int)v;
+  } else if (k == "n_stab") {
+    if (v < 1 || (double)(int)v != v) return fail(DQMC_EINVAL, "n_stab must be a positive integer");
+    c->n_stab = (int)v;
+  } else if (k == "precision") {
+    if (v != 0.0 && v != 1.0) return fail(DQMC_EINVAL, "precision must be 0 (fp64) or 1 (mixed)");
+    c->precision = (int)v;
+  } else if (k == "chain") {
+    if (v < 0 || v > 0xffffff || (double)(int)v != v) return fail(DQMC_EINVAL, "chain must be in [0, 2^24)");
+    c->chain = (int)v;
+  } else if (k == "timing") {
+    c->timing = v != 0.0;
+  } else if (k == "site_offsets") {
+    c->site_offsets = v != 0.0;
+  } else if (k == "bin") {
+    if (v < 1) return fail(DQMC_EINVAL, "bin must be >= 1");
+    c->bin = (int)v;
+  } else if (k == "drift_limit") {
+    if (!(v > 0.0)) return fail(DQMC_EINVAL, "drift_limit must be positive");
+    c->drift_limit = v;
+  } else {
+    return fail(DQMC_EINVAL, "unknown option '" + k + "'");
+  }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_stream(dqmc_ctx *c, void *stream) {
+  DQ_CHECK(check_ctx(c));
+  c->stream = static_cast<cudaStream_t>(stream);
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_allocator(dqmc_ctx *c, void *(*alloc)(size_t, void *),
+                               void (*release)(void *, void *), void *user) {
+  DQ_CHECK(check_ctx(c));
+  if (c->allocated) return fail(DQMC_ESTATE, "allocator must be set before the first allocation");
+  if ((alloc == nullptr) != (release == nullptr)) return fail(DQMC_EINVAL, "alloc and release go together");
+  c->ualloc = alloc;
+  c->ufree = release;
+  c->uuser = user;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_sweep(dqmc_ctx *c, int n_sweeps, int measure) {
+  DQ_CHECK(check_ctx(c));
+  if (n_sweeps < 0) return fail(DQMC_EINVAL, "n_sweeps must be >= 0");
+  DQ_CHECK(ensure_ready(c));
+  PhaseTimer tm(c);
+  for (int s = 0; s < n_sweeps; ++s) {
+    CK(cudaMemsetAsync(c->drift_max, 0, sizeof(double), c->stream));
+    dqmc_status st = one_sweep(c, measure != 0, tm);
+    if (st != DQMC_OK) return st;
+    st = read_status(c);
+    if (st != DQMC_OK) return st;
+    tm.collect();
+  }
+  if (measure && c->meas_n > 0) {
+    std::vector<double> h((size_t)c->meas_n * 6);
+    CK(cudaMemcpyAsync(h.data(), c->meas_obs, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < c->meas_n; ++q) {
+      std::array<double, 6> a;
+      for (int j = 0; j < 6; ++j) a[j] = h[(size_t)q * 6 + j];
+      c->samples.push_back(a);
+    }
+    c->meas_n = 0;
+  }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_green(dqmc_ctx *c, int slice, double *G_out) {
+  DQ_CHECK(check_ctx(c));
+  if (!G_out) return fail(DQMC_EINVAL, "G_out is NULL");
+  if (slice < 0 || slice > c->M) return fail(DQMC_EINVAL, "slice out of range");
+  DQ_CHECK(ensure_ready(c));
+  // right chain B(slice, 0) in tmpA, left chain B(beta, slice)^T in tmpB, QR every n_stab slices
+  DQ_CHECK(udv_identity(c, c->tmpA));
+  for (int l0 = 0; l0 < slice; l0 += c->n_stab) {
+    std::vector<int> sl;
+    for (int m = l0 + 1; m <= std::min(slice, l0 + c->n_stab); ++m) sl.push_back(m);
+    DQ_CHECK(udv_advance(c, c->tmpA, c->tmpA, sl, false));
+  }
+  DQ_CHECK(udv_identity(c, c->tmpB));
+  for (int l1 = c->M; l1 > slice; l1 -= c->n_stab) {
+    std::vector<int> sl;
+    for (int m = l1; m > std::max(slice, l1 - c->n_stab); --m) sl.push_back(m);
+    DQ_CHECK(udv_advance(c, c->tmpB, c->tmpB, sl, true));
+  }
+  DQ_CHECK(combine(c, c->tmpA, c->tmpB, c->Xp));
+  CK(cudaMemcpyAsync(G_out, c->Xp, (size_t)c->N * c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_get_running_green(dqmc_ctx *c, double *G_out, int *slice) {
+  DQ_CHECK(check_ctx(c));
+  if (!G_out) return fail(DQMC_EINVAL, "G_out is NULL");
+  DQ_CHECK(ensure_ready(c));
+  const size_t NN = (size_t)c->N * c->N;
+  if (c->precision == 0) {
+    CK(cudaMemcpyAsync(G_out, c->G64, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    CK(convert_f32_to_f64(c->G32, c->X, (long)NN, c->stream));
+    CK(cudaMemcpyAsync(G_out, c->X, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (slice) *slice = c->cur_slice;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_measure(dqmc_ctx *c, dqmc_obs *o) {
+  DQ_CHECK(check_ctx(c));
+  if (!o) return fail(DQMC_EINVAL, "out is NULL");
+  std::memset(o, 0, sizeof(*o));
+  const long n = (long)c->samples.size();
+  o->n_samples = n;
+  const int bs = std::max(1, c->bin);
+  const long nb = n / bs;
+  o->n_bins = nb;
+  double mean[6] = {0, 0, 0, 0, 0, 0};
+  for (const auto &a : c->samples)
+    for (int j = 0; j < 6; ++j) mean[j] += a[j];
+  for (int j = 0; j < 6; ++j) mean[j] = n ? mean[j] / n : std::nan("");
+  o->S_pair_G = mean[0];
+  o->S_pair_dk = mean[1];
+  o->phi2_G = mean[2];
+  o->phi2_K = mean[3];
+  o->density = mean[4];
+  o->ekin = mean[5];
+  std::vector<std::array<double, 6>> bins(nb);
+  for (long b = 0; b < nb; ++b) {
+    for (int j = 0; j < 6; ++j) {
+      double s = 0;
+      for (int q = 0; q < bs; ++q) s += c->samples[b * bs + q][j];
+      bins[b][j] = s / bs;
+    }
+  }
+  for (int j = 0; j < 6; ++j) {
+    if (nb < 2) {
+      o->err[j] = std::nan("");
+      continue;
+    }
+    double m = 0, v = 0;
+    for (long b = 0; b < nb; ++b) m += bins[b][j];
+    m /= nb;
+    for (long b = 0; b < nb; ++b) v += (bins[b][j] - m) * (bins[b][j] - m);
+    o->err[j] = std::sqrt(v / (nb - 1) / nb);
+  }
+  // jackknife over bins for R_pair and P
+  const double N = c->N;
+  auto Rf = [&](double sG, double sdk) { return 1.0 - sdk / sG; };
+  auto Pf = [&](double sG) { return std::sqrt(sG / N); };
+  o->R_pair = Rf(mean[0], mean[1]);
+  o->P = Pf(mean[0]);
+  o->D_G = std::sqrt(mean[2]);
+  o->D_K = std::sqrt(mean[3]);
+  if (nb >= 2) {
+    double tot0 = 0, tot1 = 0;
+    for (long b = 0; b < nb; ++b) {
+      tot0 += bins[b][0];
+      tot1 += bins[b][1];
+    }
+    std::vector<double> jr(nb), jp(nb);
+    double mr = 0, mp = 0;
+    for (long b = 0; b < nb; ++b) {
+      const double s0 = (tot0 - bins[b][0]) / (nb - 1), s1 = (tot1 - bins[b][1]) / (nb - 1);
+      jr[b] = Rf(s0, s1);
+      jp[b] = Pf(s0);
+      mr += jr[b];
+      mp += jp[b];
+    }
+    mr /= nb;
+    mp /= nb;
+    double vr = 0, vp = 0;
+    for (long b = 0; b < nb; ++b) {
+      vr += (jr[b] - mr) * (jr[b] - mr);
+      vp += (jp[b] - mp) * (jp[b] - mp);
+    }
+    o->R_pair_err = std::sqrt((nb - 1.0) / nb * vr);
+    o->P_err = std::sqrt((nb - 1.0) / nb * vp);
+  } else {
+    o->R_pair_err = std::nan("");
+    o->P_err = std::nan("");
+  }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_get_stats(dqmc_ctx *c, dqmc_stats *o) {
+  if (!c) return fail(DQMC_EINVAL, "null context");
+  if (!o) return fail(DQMC_EINVAL, "out is NULL");
+  o->sweeps = c->sweeps;
+  o->proposed = c->proposed;
+  o->accepted = c->accepted;
+  o->max_drift = c->max_drift;
+  o->last_drift = c->last_drift;
+  o->ms_wrap = c->ms_wrap;
+  o->ms_update = c->ms_update;
+  o->ms_stab = c->ms_stab;
+  o->ms_measure = c->ms_measure;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_get_field(dqmc_ctx *c, int8_t *s_out) {
+  DQ_CHECK(check_ctx(c));
+  if (!s_out) return fail(DQMC_EINVAL, "s_out is NULL");
+  DQ_CHECK(ensure_alloc(c));
+  CK(cudaMemcpyAsync(s_out, c->field, (size_t)c->M * c->N, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_set_field(dqmc_ctx *c, const int8_t *s) {
+  DQ_CHECK(check_ctx(c));
+  if (!s) return fail(DQMC_EINVAL, "s is NULL");
+  const size_t n = (size_t)c->M * c->N;
+  for (size_t q = 0; q < n; ++q)
+    if (s[q] != 1 && s[q] != -1) return fail(DQMC_EINVAL, "field values must be +1 or -1");
+  DQ_CHECK(ensure_alloc(c));
+  CK(cudaMemcpyAsync(c->field, s, n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->ready = false;
+  return ensure_ready(c);
+}
+
+dqmc_status dqmc_save(dqmc_ctx *c, const char *path) {
+  DQ_CHECK(check_ctx(c));
+  if (!path) return fail(DQMC_EINVAL, "path is NULL");
+  DQ_CHECK(ensure_alloc(c));
+  std::vector<int8_t> f((size_t)c->M * c->N);
+  CK(cudaMemcpyAsync(f.data(), c->field, f.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  FILE *fp = std::fopen(path, "wb");
+  if (!fp) return fail(DQMC_EINVAL, std::string("cannot open ") + path);
+  const char magic[8] = {'D', 'Q', 'M', 'C', 'G', 'B', '3', '1'};
+  double par[5] = {(double)c->L, c->beta, c->dtau, c->U, c->mu};
+  int opt[7] = {c->k, c->n_stab, c->precision, c->chain, c->site_offsets, c->bin, 0};
+  long st[3] = {c->sweeps, c->proposed, c->accepted};
+  long ns = (long)c->samples.size();
+  bool ok = std::fwrite(magic, 1, 8, fp) == 8 && std::fwrite(par, sizeof(double), 5, fp) == 5 &&
+            std::fwrite(&c->seed, sizeof(uint64_t), 1, fp) == 1 &&
+            std::fwrite(opt, sizeof(int), 7, fp) == 7 && std::fwrite(st, sizeof(long), 3, fp) == 3 &&
+            std::fwrite(&c->max_drift, sizeof(double), 1, fp) == 1 &&
+            std::fwrite(f.data(), 1, f.size(), fp) == f.size() &&
+            std::fwrite(&ns, sizeof(long), 1, fp) == 1;
+  for (long q = 0; ok && q < ns; ++q) ok = std::fwrite(c->samples[q].data(), sizeof(double), 6, fp) == 6;
+  std::fclose(fp);
+  if (!ok) return fail(DQMC_EINVAL, "short write");
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_load(dqmc_ctx *c, const char *path) {
+  DQ_CHECK(check_ctx(c));
+  if (!path) return fail(DQMC_EINVAL, "path is NULL");
+  FILE *fp = std::fopen(path, "rb");
+  if (!fp) return fail(DQMC_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  double par[5];
+  uint64_t seed;
+  int opt[7];
+  long st[3], ns = 0;
+  double md;
+  bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "DQMCGB31", 8) == 0 &&
+            std::fread(par, sizeof(double), 5, fp) == 5 && std::fread(&seed, sizeof(uint64_t), 1, fp) == 1 &&
+            std::fread(opt, sizeof(int), 7, fp) == 7 && std::fread(st, sizeof(long), 3, fp) == 3 &&
+            std::fread(&md, sizeof(double), 1, fp) == 1;
+  if (!ok) {
+    std::fclose(fp);
+    return fail(DQMC_EINVAL, "not a checkpoint file");
+  }
+  if ((int)par[0] != c->L || par[1] != c->beta || par[2] != c->dtau || par[3] != c->U || par[4] != c->mu) {
+    std::fclose(fp);
+    return fail(DQMC_EINVAL, "checkpoint parameters do not match this context");
+  }
+  if (c->allocated && (opt[0] != c->k || opt[1] != c->n_stab || opt[2] != c->precision || opt[3] != c->chain)) {
+    std::fclose(fp);
+    return fail(DQMC_ESTATE, "checkpoint options differ from an already started context");
+  }
+  std::vector<int8_t> f((size_t)c->M * c->N);
+  ok = std::fread(f.data(), 1, f.size(), fp) == f.size() && std::fread(&ns, sizeof(long), 1, fp) == 1;
+  std::vector<std::array<double, 6>> smp(ok ? ns : 0);
+  for (long q = 0; ok && q < ns; ++q) ok = std::fread(smp[q].data(), sizeof(double), 6, fp) == 6;
+  std::fclose(fp);
+  if (!ok) return fail(DQMC_EINVAL, "truncated checkpoint");
+  if (!c->allocated) {
+    c->k = opt[0];
+    c->n_stab = opt[1];
+    c->precision = opt[2];
+    c->chain = opt[3];
+  }
+  c->seed = seed;
+  c->site_offsets = opt[4];
+  c->bin = opt[5];
+  DQ_CHECK(ensure_alloc(c));
+  CK(cudaMemcpyAsync(c->field, f.data(), f.size(), cudaMemcpyHostToDevice, c->stream));
+  unsigned long long acc = (unsigned long long)st[2];
+  CK(cudaMemcpyAsync(c->total_acc, &acc, sizeof(acc), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->sweeps = st[0];
+  c->proposed = st[1];
+  c->accepted = st[2];
+  c->max_drift = md;
+  c->samples = smp;
+  c->ready = false;
+  return ensure_ready(c);
+}
+
+void dqmc_destroy(dqmc_ctx *c) {
+  if (!c) return;
+  if (c->allocated || !c->allocs.empty()) cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs) {
+    if (c->ufree)
+      c->ufree(p, c->uuser);
+    else
+      cudaFree(p);
+  }
+  delete c;
+}
+
+}  // extern "C"

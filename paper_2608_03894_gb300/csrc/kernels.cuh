@@ -1,0 +1,59 @@
+// Launch interfaces of the hot-path kernels (propagation, delayed update,
+// measurement), shared by the engine and the operator entry points.
+#pragma once
+
+#include "common.cuh"
+
+namespace dq {
+
+// ---- FFT propagator (prop_f32.cu / prop_f64.cu)
+cudaError_t launch_prop_f64(int L, int side, const double *X, double *Y, int nvec, int ld,
+                            const cpx<double> *E, const double *pre, const double *post,
+                            const double *vscale, cudaStream_t st);
+cudaError_t launch_prop_f32(int L, int side, const float *X, float *Y, int nvec, int ld,
+                            const cpx<float> *E, const float *pre, const float *post,
+                            const float *vscale, cudaStream_t st);
+
+// ---- delayed update (update.cu)
+template <typename T>
+cudaError_t launch_gather(int N, int s0, int kb, int K, const T *G, T *Gcol, T *Grow,
+                          cudaStream_t st);
+
+struct MetroArgs {
+  int N, s0, kb, K;
+  int ld_g;              // row stride of g = G[S, S]
+  double e2l, em2l;      // e^{2 lambda}, e^{-2 lambda} (host-computed)
+  uint32_t k0, k1;       // Philox key (seed)
+  uint32_t c2, c3;       // counter words 2 (2*sweep + pass) and 3 (chain | domain << 24)
+  int slice0;            // counter word 1 (0-based slice)
+};
+template <typename TG>
+cudaError_t launch_metropolis(const MetroArgs &a, const TG *g, int8_t *s, const uint8_t *forced,
+                              double *Gamma, int *accept_count, int *status,
+                              unsigned long long *total, cudaStream_t st);
+
+struct FlushArgs {
+  int N, s0, kb;   // current block
+  int ns0, nkb;    // next block (nkb = 0: none)
+  int rows_per_cta;
+};
+template <typename T>
+cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
+                         const double *Gamma, const int *acc, T *Gcol_next, T *Grow_next,
+                         cudaStream_t st);
+
+// ---- measurement (measure.cu)
+struct MeasTables {
+  const double *pc, *ps;    // e^{i Q r} for Q = Gamma + dk
+  const double *wgc, *wgs;  // CDW weights at Gamma
+  const double *wkc, *wks;  // CDW weights at K (nullptr if absent)
+  const int *nbr;           // 4 neighbours per site (with repeats for tiny tori)
+};
+constexpr int kMeasRaw = 10;
+cudaError_t launch_measure(const double *G, int N, const MeasTables &t, double *raw, double thop,
+                           double *obs, cudaStream_t st);
+
+// ---- shared-memory opt-in, once per (kernel, device)
+cudaError_t ensure_smem_attr(const void *func, int bytes);
+
+}  // namespace dq

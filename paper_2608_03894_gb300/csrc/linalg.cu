@@ -1,0 +1,698 @@
+// FP64 dense linear algebra for the UDV stabilisation.
+//
+// The stabilisation (not in the paper; standard DQMC practice) needs QR
+// factorisations of N x N matrices, explicit Q factors, Q^T applied to a
+// matrix and triangular solves, all in FP64. Blocked Householder QR: a panel
+// of nb columns is factorised by one 8-CTA thread-block cluster whose CTAs
+// each hold a slice of the panel rows in shared memory and combine their
+// partial column dot products through distributed shared memory; the
+// trailing update is two GEMMs with the compact-WY factors V and
+// Y = V T^T (Q_panel = I - V T V^T).
+#include <cooperative_groups.h>
+
+#include "linalg.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dq {
+
+// ====================================================================== GEMM
+// 64 x 64 tile, BK = 16, 256 threads, 4 x 4 outputs per thread (rows ty+16i,
+// columns tx+16j). DFMA throughput bound on GB300; the tile keeps operand
+// reuse at 16 FMAs per 8 shared loads.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256)
+    dgemm_kernel(int M, int N, int K, double alpha, const double *__restrict__ A, int lda,
+                 const double *__restrict__ B, int ldb, double beta, double *__restrict__ C,
+                 int ldc, const double *__restrict__ rs, const double *__restrict__ cs, int klen,
+                 int atomic) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int kbeg = blockIdx.z * klen;
+  const int kend = min(K, kbeg + klen);
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int e = tid; e < BM * BK; e += 256) {
+      int mm, kk;
+      if (!TA) {
+        kk = e % BK;
+        mm = e / BK;
+      } else {
+        mm = e % BM;
+        kk = e / BM;
+      }
+      const int gm = m0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gm < M && gk < kend) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+      As[kk][mm] = v;
+    }
+#pragma unroll
+    for (int e = tid; e < BN * BK; e += 256) {
+      int nn, kk;
+      if (!TB) {
+        nn = e % BN;
+        kk = e / BN;
+      } else {
+        kk = e % BK;
+        nn = e / BK;
+      }
+      const int gn = n0 + nn, gk = k0 + kk;
+      double v = 0.0;
+      if (gn < N && gk < kend) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+    const double r = rs ? rs[gm] : 1.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      const double v = alpha * r * acc[i][j] * (cs ? cs[gn] : 1.0);
+      double *cp = C + (size_t)gm * ldc + gn;
+      if (atomic)
+        atomicAdd(cp, v);
+      else
+        *cp = (beta != 0.0) ? v + beta * (*cp) : v;
+    }
+  }
+}
+
+__global__ void scale_matrix_kernel(double *C, int M, int N, int ldc, double beta) {
+  const long total = (long)M * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    double *p = C + (size_t)i * ldc + j;
+    *p = (beta == 0.0) ? 0.0 : beta * (*p);
+  }
+}
+
+static int grid_for(long work, int per = 256) {
+  long g = (work + per - 1) / per;
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
+                  const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
+                  const double *cs, cudaStream_t st, int splitk) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K <= 0) {
+    scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
+    return cudaGetLastError();
+  }
+  const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+  if (splitk <= 0) {
+    // aim for ~2 waves over 152 SMs, each split at least 128 deep
+    splitk = 1;
+    if (tiles < 304) {
+      splitk = (304 + tiles - 1) / tiles;
+      const int maxs = (K + 127) / 128;
+      if (splitk > maxs) splitk = maxs;
+      if (splitk < 1) splitk = 1;
+    }
+  }
+  int klen = (K + splitk - 1) / splitk;
+  klen = ((klen + 15) / 16) * 16;
+  splitk = (K + klen - 1) / klen;
+  const int atomic = splitk > 1;
+  if (atomic) {
+    scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
+  }
+  dim3 grid((N + 63) / 64, (M + 63) / 64, splitk);
+  if (!ta && !tb)
+    dgemm_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
+  else if (ta && !tb)
+    dgemm_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
+  else if (!ta && tb)
+    dgemm_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
+  else
+    dgemm_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
+  return cudaGetLastError();
+}
+
+// ====================================================================== QR panel
+constexpr int kClusterCTAs = 8;
+
+int qr_panel_width(int n) {
+  // nb = 64 when a 1/8 slice of the panel rows plus the nb x nb Gram/T
+  // buffers fit in shared memory, else 32
+  const int rows_per = (n + kClusterCTAs - 1) / kClusterCTAs;
+  const size_t need64 = ((size_t)rows_per * 65 + 3 * 64 * 64 + 16 * 64 + 64) * sizeof(double);
+  return need64 <= 220 * 1024 ? 64 : 32;
+}
+
+static size_t qr_panel_smem(int n, int nb) {
+  const int rows_per = (n + kClusterCTAs - 1) / kClusterCTAs;
+  return ((size_t)rows_per * (nb + 1) + 3 * (size_t)nb * nb + 16 * (size_t)nb + 64) * sizeof(double);
+}
+
+size_t qr_work_doubles(int n) {
+  const int nb = qr_panel_width(n);
+  const int nblk = (n + nb - 1) / nb;
+  return 3 * (size_t)n * n + (size_t)n + (size_t)nb * n + (size_t)nblk * nb * nb;
+}
+
+void qr_work_bind(QRWork &w, int n, double *mem) {
+  w.n = n;
+  w.nb = qr_panel_width(n);
+  const int nblk = (n + w.nb - 1) / w.nb;
+  w.V = mem;
+  w.Y = w.V + (size_t)n * n;
+  w.Y2 = w.Y + (size_t)n * n;
+  w.tau = w.Y2 + (size_t)n * n;
+  w.W = w.tau + n;
+  w.Rinv = w.W + (size_t)w.nb * n;
+  (void)nblk;
+}
+
+// Factorises the panel A[p:n, p:p+nc] (nc <= NB) in place. Rows are split
+// over the 8 CTAs of the cluster; CTA r owns panel rows [r R, (r+1) R).
+// Per column jj: every CTA forms partial dot products of the column with the
+// remaining panel columns over its rows, the cluster combines them through
+// DSMEM, every CTA computes the same reflector (LAPACK convention:
+// H = I - tau v v^T, v_0 = 1, H x = beta e_1) and updates its own rows.
+// Afterwards: V explicit, T from the Gram matrix V^T V by the standard
+// recurrence, Y = V T^T and Y2 = V T.
+template <int NB>
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
+    qr_panel_kernel(double *A, int n, int p, int nc, double *V, double *Y, double *Y2,
+                    double *tau_out) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int m = n - p;
+  const int rows_per = (m + kClusterCTAs - 1) / kClusterCTAs;
+  const int lr0 = rank * rows_per;
+  const int myrows = max(0, min(m, lr0 + rows_per) - lr0);
+  constexpr int LDP = NB + 1;
+  extern __shared__ __align__(16) double sm[];
+  double *P = sm;                            // rows_per x LDP
+  double *red = P + (size_t)rows_per * LDP;  // 8 x NB
+  double *part = red + 8 * NB;               // 2 x NB
+  double *piv = part + 2 * NB;               // 2 x NB
+  double *sD = piv + 2 * NB;                 // NB
+  double *sy0 = sD + NB;                     // NB
+  double *sw = sy0 + NB;                     // NB
+  double *stau = sw + NB;                    // NB
+  double *Gm = stau + NB;                    // NB x NB (partial Gram)
+  double *Gs = Gm + NB * NB;                 // NB x NB (summed Gram, rank 0)
+  double *Tm = Gs + NB * NB;                 // NB x NB (T)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int e = tid; e < myrows * NB; e += 256) {
+    const int r = e / NB, c = e % NB;
+    P[r * LDP + c] = (c < nc) ? A[(size_t)(p + lr0 + r) * n + p + c] : 0.0;
+  }
+  __syncthreads();
+
+  for (int jj = 0; jj < nc; ++jj) {
+    const int buf = jj & 1;
+    const int owner = jj / rows_per;
+    for (int c = lane; c < NB; c += 32) {
+      double acc = 0.0;
+      if (c >= jj && c < nc) {
+        for (int r = warp; r < myrows; r += 8)
+          if (lr0 + r > jj) acc = fma(P[r * LDP + jj], P[r * LDP + c], acc);
+      }
+      red[warp * NB + c] = acc;
+    }
+    if (rank == owner)
+      for (int c = tid; c < NB; c += 256) piv[buf * NB + c] = P[(jj - lr0) * LDP + c];
+    __syncthreads();
+    if (tid < NB) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) s += red[w * NB + tid];
+      part[buf * NB + tid] = s;
+    }
+    cluster.sync();
+    if (tid < NB) {
+      double D = 0.0;
+      for (int r2 = 0; r2 < kClusterCTAs; ++r2) {
+        const double *rp = cluster.map_shared_rank(part, r2);
+        D += rp[buf * NB + tid];
+      }
+      const double *op = cluster.map_shared_rank(piv, owner);
+      sD[tid] = D;
+      sy0[tid] = op[buf * NB + tid];
+    }
+    __syncthreads();
+    const double alpha = sy0[jj], sigma = sD[jj];
+    double tau = 0.0, beta = alpha, scal = 0.0;
+    if (sigma > 0.0) {
+      const double nrm = sqrt(alpha * alpha + sigma);
+      beta = (alpha >= 0.0) ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    if (tid < NB) sw[tid] = (tid > jj && tid < nc) ? sy0[tid] + scal * sD[tid] : 0.0;
+    if (tid == 0) stau[jj] = tau;
+    __syncthreads();
+    for (int r = tid; r < myrows; r += 256) {
+      const int lr = lr0 + r;
+      double *row = P + r * LDP;
+      if (lr > jj) {
+        const double v = row[jj] * scal;
+        const double tv = tau * v;
+        for (int c = jj + 1; c < nc; ++c) row[c] = fma(-tv, sw[c], row[c]);
+        row[jj] = v;
+      } else if (lr == jj) {
+        for (int c = jj + 1; c < nc; ++c) row[c] = fma(-tau, sw[c], row[c]);
+        row[jj] = beta;
+      }
+    }
+    __syncthreads();
+  }
+
+  // write back R / V into A, explicit V, and the partial Gram V^T V
+  for (int e = tid; e < myrows * nc; e += 256) {
+    const int r = e / nc, c = e % nc;
+    const int lr = lr0 + r;
+    const double pv = P[r * LDP + c];
+    A[(size_t)(p + lr) * n + p + c] = pv;
+    V[(size_t)(p + lr) * n + p + c] = (lr > c) ? pv : (lr == c ? 1.0 : 0.0);
+  }
+  for (int e = tid; e < NB * NB; e += 256) {
+    const int a = e / NB, b = e % NB;
+    double acc = 0.0;
+    if (a < nc && b < nc) {
+      for (int r = 0; r < myrows; ++r) {
+        const int lr = lr0 + r;
+        const double va = (lr > a) ? P[r * LDP + a] : (lr == a ? 1.0 : 0.0);
+        const double vb = (lr > b) ? P[r * LDP + b] : (lr == b ? 1.0 : 0.0);
+        acc = fma(va, vb, acc);
+      }
+    }
+    Gm[e] = acc;
+  }
+  cluster.sync();
+  if (rank == 0) {
+    for (int e = tid; e < NB * NB; e += 256) {
+      double s = 0.0;
+      for (int r2 = 0; r2 < kClusterCTAs; ++r2) s += cluster.map_shared_rank(Gm, r2)[e];
+      Gs[e] = s;
+      Tm[e] = 0.0;
+    }
+    __syncthreads();
+    // T upper triangular: T_jj = tau_j, T[0:j, j] = -tau_j T[0:j,0:j] Gram[0:j, j]
+    for (int j = 0; j < nc; ++j) {
+      if (tid < j) {
+        double acc = 0.0;
+        for (int k = tid; k < j; ++k) acc = fma(Tm[tid * NB + k], Gs[k * NB + j], acc);
+        Tm[tid * NB + j] = -stau[j] * acc;
+      }
+      if (tid == j) Tm[j * NB + j] = stau[j];
+      __syncthreads();
+    }
+    for (int j = tid; j < nc; j += 256) tau_out[p + j] = stau[j];
+  }
+  cluster.sync();
+  if (rank != 0) {
+    const double *T0 = cluster.map_shared_rank(Tm, 0);
+    for (int e = tid; e < NB * NB; e += 256) Tm[e] = T0[e];
+  }
+  __syncthreads();
+  // Y = V T^T, Y2 = V T for my rows
+  for (int e = tid; e < myrows * nc; e += 256) {
+    const int r = e / nc, a = e % nc;
+    const int lr = lr0 + r;
+    double y = 0.0, y2 = 0.0;
+    for (int b = 0; b < nc; ++b) {
+      const double vb = (lr > b) ? P[r * LDP + b] : (lr == b ? 1.0 : 0.0);
+      y = fma(vb, Tm[a * NB + b], y);
+      y2 = fma(vb, Tm[b * NB + a], y2);
+    }
+    Y[(size_t)(p + lr) * n + p + a] = y;
+    Y2[(size_t)(p + lr) * n + p + a] = y2;
+  }
+  cluster.sync();
+}
+
+template <int NB>
+static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, cudaStream_t st) {
+  const size_t smem = qr_panel_smem(n, NB);
+  cudaError_t e = cudaFuncSetAttribute(qr_panel_kernel<NB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  qr_panel_kernel<NB><<<kClusterCTAs, 256, smem, st>>>(A, n, p, nc, w.V, w.Y, w.Y2, w.tau);
+  return cudaGetLastError();
+}
+
+cudaError_t qr_factor(double *A, int n, QRWork &w, cudaStream_t st) {
+  const int nb = w.nb;
+  for (int p = 0; p < n; p += nb) {
+    const int nc = min(nb, n - p);
+    cudaError_t e = (nb == 64) ? launch_qr_panel<64>(A, n, p, nc, w, st)
+                               : launch_qr_panel<32>(A, n, p, nc, w, st);
+    if (e != cudaSuccess) return e;
+    const int ntr = n - p - nc;
+    if (ntr > 0) {
+      // W = V_p^T A[p:, p+nc:]  (nc x ntr, K = n - p)
+      e = dgemm(true, false, nc, ntr, n - p, 1.0, w.V + (size_t)p * n + p, n,
+                A + (size_t)p * n + p + nc, n, 0.0, w.W, ntr, nullptr, nullptr, st);
+      if (e != cudaSuccess) return e;
+      // A[p:, p+nc:] -= Y_p W
+      e = dgemm(false, false, n - p, ntr, nc, -1.0, w.Y + (size_t)p * n + p, n, w.W, ntr, 1.0,
+                A + (size_t)p * n + p + nc, n, nullptr, nullptr, st, 1);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t qr_form_q(double *Q, int n, QRWork &w, cudaStream_t st) {
+  cudaError_t e = set_identity(Q, n, n, st);
+  if (e != cudaSuccess) return e;
+  const int nb = w.nb;
+  const int last = ((n - 1) / nb) * nb;
+  for (int p = last; p >= 0; p -= nb) {
+    const int nc = min(nb, n - p);
+    const int cols = n - p;
+    e = dgemm(true, false, nc, cols, n - p, 1.0, w.V + (size_t)p * n + p, n,
+              Q + (size_t)p * n + p, n, 0.0, w.W, cols, nullptr, nullptr, st);
+    if (e != cudaSuccess) return e;
+    e = dgemm(false, false, n - p, cols, nc, -1.0, w.Y2 + (size_t)p * n + p, n, w.W, cols, 1.0,
+              Q + (size_t)p * n + p, n, nullptr, nullptr, st, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t qr_apply_qt(double *B, int n, int ncols, int ldb, QRWork &w, cudaStream_t st) {
+  const int nb = w.nb;
+  for (int p = 0; p < n; p += nb) {
+    const int nc = min(nb, n - p);
+    cudaError_t e = dgemm(true, false, nc, ncols, n - p, 1.0, w.V + (size_t)p * n + p, n,
+                          B + (size_t)p * ldb, ldb, 0.0, w.W, ncols, nullptr, nullptr, st);
+    if (e != cudaSuccess) return e;
+    e = dgemm(false, false, n - p, ncols, nc, -1.0, w.Y + (size_t)p * n + p, n, w.W, ncols, 1.0,
+              B + (size_t)p * ldb, ldb, nullptr, nullptr, st, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Inverse of each nb x nb upper-triangular diagonal block of R (in A).
+// One CTA per block; thread j solves column j of U X = I by back substitution.
+__global__ void tri_inv_upper_blocks_kernel(const double *A, int n, int nb, double *Rinv) {
+  const int b = blockIdx.x;
+  const int p = b * nb;
+  const int bs = min(nb, n - p);
+  extern __shared__ double su[];  // bs x bs
+  for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+    const int i = e / bs, j = e % bs;
+    su[e] = A[(size_t)(p + i) * n + p + j];
+  }
+  __syncthreads();
+  double *X = Rinv + (size_t)b * nb * nb;
+  const int j = threadIdx.x;
+  if (j < nb) {
+    for (int i = 0; i < nb; ++i) X[i * nb + j] = 0.0;
+  }
+  if (j < bs) {
+    X[j * nb + j] = 1.0 / su[j * bs + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s = fma(su[i * bs + k], X[k * nb + j], s);
+      X[i * nb + j] = -s / su[i * bs + i];
+    }
+  }
+}
+
+cudaError_t qr_solve_r(const double *A, int n, double *B, double *Z, int ncols, QRWork &w,
+                       cudaStream_t st) {
+  const int nb = w.nb;
+  const int nblk = (n + nb - 1) / nb;
+  tri_inv_upper_blocks_kernel<<<nblk, 64, (size_t)nb * nb * sizeof(double), st>>>(A, n, nb, w.Rinv);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int p = b * nb;
+    const int bs = min(nb, n - p);
+    // Z[p:p+bs] = Rinv_b B[p:p+bs]
+    e = dgemm(false, false, bs, ncols, bs, 1.0, w.Rinv + (size_t)b * nb * nb, nb,
+              B + (size_t)p * ncols, ncols, 0.0, Z + (size_t)p * ncols, ncols, nullptr, nullptr,
+              st, 1);
+    if (e != cudaSuccess) return e;
+    if (p > 0) {
+      // B[0:p] -= R[0:p, p:p+bs] Z[p:p+bs]
+      e = dgemm(false, false, p, ncols, bs, -1.0, A + p, n, Z + (size_t)p * ncols, ncols, 1.0, B,
+                ncols, nullptr, nullptr, st, 1);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// ====================================================================== helpers
+__global__ void set_identity_kernel(double *A, int n, int ld) {
+  const long total = (long)n * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    A[(size_t)i * ld + j] = (i == j) ? 1.0 : 0.0;
+  }
+}
+cudaError_t set_identity(double *A, int n, int ld, cudaStream_t st) {
+  set_identity_kernel<<<grid_for((long)n * n), 256, 0, st>>>(A, n, ld);
+  return cudaGetLastError();
+}
+
+__global__ void set_value_kernel(double *x, long n, double v) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    x[e] = v;
+}
+cudaError_t set_value(double *x, long n, double v, cudaStream_t st) {
+  set_value_kernel<<<grid_for(n), 256, 0, st>>>(x, n, v);
+  return cudaGetLastError();
+}
+
+// 32 x 32 tiled transpose with row scaling of the output
+__global__ void transpose_scale_kernel(const double *in, int ld, double *out, int n,
+                                       const double *rs) {
+  __shared__ double t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = by + r, j = bx + threadIdx.x;
+    t[r][threadIdx.x] = (i < n && j < n) ? in[(size_t)i * ld + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = bx + r, j = by + threadIdx.x;  // out[i][j] = in[j][i]
+    if (i < n && j < n) out[(size_t)i * n + j] = t[threadIdx.x][r] * (rs ? rs[i] : 1.0);
+  }
+}
+cudaError_t transpose_scale(const double *in, int ld, double *out, int n, const double *rs,
+                            cudaStream_t st) {
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  transpose_scale_kernel<<<grid, block, 0, st>>>(in, ld, out, n, rs);
+  return cudaGetLastError();
+}
+
+__global__ void scale_rows_cols_kernel(double *X, int n, int ld, const double *rs, const double *cs) {
+  const long total = (long)n * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    double v = X[(size_t)i * ld + j];
+    if (rs) v *= rs[i];
+    if (cs) v *= cs[j];
+    X[(size_t)i * ld + j] = v;
+  }
+}
+cudaError_t scale_rows_cols(double *X, int n, int ld, const double *rs, const double *cs,
+                            cudaStream_t st) {
+  scale_rows_cols_kernel<<<grid_for((long)n * n), 256, 0, st>>>(X, n, ld, rs, cs);
+  return cudaGetLastError();
+}
+
+__global__ void column_norms_kernel(const double *X, int n, const double *D, double *norms) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double v = X[(size_t)i * n + j];
+    s = fma(v, v, s);
+  }
+  norms[j] = sqrt(s) * (D ? D[j] : 1.0);
+}
+cudaError_t column_norms_scaled(const double *X, int n, const double *D, double *norms,
+                                cudaStream_t st) {
+  column_norms_kernel<<<(n + 127) / 128, 128, 0, st>>>(X, n, D, norms);
+  return cudaGetLastError();
+}
+
+// Bitonic sort of (key desc, index asc) in one CTA.
+__global__ void argsort_desc_kernel(const double *key, int n, int npow2, int *perm) {
+  extern __shared__ unsigned char raw[];
+  double *k = reinterpret_cast<double *>(raw);
+  int *ix = reinterpret_cast<int *>(k + npow2);
+  // real keys are norms >= 0 (NaN mapped to -0.5); padding is -inf, so the
+  // first n sorted entries are always real indices < n
+  for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+    const double kv = (i < n) ? key[i] : 0.0;
+    k[i] = (i < n) ? (kv != kv ? -0.5 : kv) : -1.0 / 0.0;
+    ix[i] = i;
+  }
+  __syncthreads();
+  for (int size = 2; size <= npow2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+        const int jx = i ^ stride;
+        if (jx > i) {
+          // "before(a, b)": a sorts before b if key larger, ties by smaller index
+          const bool up = ((i & size) == 0);
+          const bool i_before_j = (k[i] > k[jx]) || (k[i] == k[jx] && ix[i] < ix[jx]);
+          if (up != i_before_j) {
+            const double tk = k[i];
+            k[i] = k[jx];
+            k[jx] = tk;
+            const int ti = ix[i];
+            ix[i] = ix[jx];
+            ix[jx] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = ix[i];
+}
+cudaError_t argsort_desc(const double *key, int n, int *perm, cudaStream_t st) {
+  int np = 1;
+  while (np < n) np <<= 1;
+  if (np > 8192) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)np * (sizeof(double) + sizeof(int));
+  cudaError_t e = cudaFuncSetAttribute(argsort_desc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  argsort_desc_kernel<<<1, 1024, smem, st>>>(key, n, np, perm);
+  return cudaGetLastError();
+}
+
+__global__ void permute_udv_kernel(const double *X, const double *D, const double *T,
+                                   const int *perm, int n, double *Xp, double *Dp, double *Tp) {
+  const long total = (long)n * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), c = (int)(e % n);
+    Xp[e] = X[(size_t)i * n + perm[c]];
+    Tp[e] = T[(size_t)perm[i] * n + c];
+    if (i == 0) Dp[c] = D[perm[c]];
+  }
+}
+cudaError_t permute_udv(const double *X, const double *D, const double *T, const int *perm, int n,
+                        double *Xp, double *Dp, double *Tp, cudaStream_t st) {
+  permute_udv_kernel<<<grid_for((long)n * n), 256, 0, st>>>(X, D, T, perm, n, Xp, Dp, Tp);
+  return cudaGetLastError();
+}
+
+__global__ void udv_diag_kernel(const double *R, int n, const double *Dp, double *Dnew) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Dnew[i] = fabs(R[(size_t)i * n + i]) * Dp[i];
+}
+__global__ void udv_scale_kernel(double *R, int n, const double *Dp, const double *Dnew) {
+  const long total = (long)n * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    R[e] = (j >= i) ? R[e] * (Dp[j] / Dnew[i]) : 0.0;
+  }
+}
+cudaError_t udv_diag_and_scale(double *R, int n, const double *Dp, double *Dnew, cudaStream_t st) {
+  udv_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(R, n, Dp, Dnew);
+  udv_scale_kernel<<<grid_for((long)n * n), 256, 0, st>>>(R, n, Dp, Dnew);
+  return cudaGetLastError();
+}
+
+template <typename TB>
+__global__ void max_abs_diff_kernel(const double *A, const TB *B, long total, double *out) {
+  double mx = 0.0;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const double d = fabs(A[e] - (double)B[e]);
+    mx = (d > mx || d != d) ? d : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = (v > mx || v != v) ? v : mx;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative doubles order like their bit patterns; NaN maps above +inf
+    const unsigned long long bits = (mx != mx) ? 0x7ff8000000000000ull
+                                               : (unsigned long long)__double_as_longlong(mx);
+    atomicMax(reinterpret_cast<unsigned long long *>(out), bits);
+  }
+}
+cudaError_t max_abs_diff_f64(const double *A, const double *B, int n, double *out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  max_abs_diff_kernel<double><<<grid_for((long)n * n, 1024), 256, 0, st>>>(A, B, (long)n * n, out);
+  return cudaGetLastError();
+}
+cudaError_t max_abs_diff_f32(const double *A, const float *B, int n, double *out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  max_abs_diff_kernel<float><<<grid_for((long)n * n, 1024), 256, 0, st>>>(A, B, (long)n * n, out);
+  return cudaGetLastError();
+}
+
+__global__ void f64_to_f32_kernel(const double *A, float *B, long n) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    B[e] = (float)A[e];
+}
+__global__ void f32_to_f64_kernel(const float *A, double *B, long n) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    B[e] = (double)A[e];
+}
+cudaError_t convert_f64_to_f32(const double *A, float *B, long n, cudaStream_t st) {
+  f64_to_f32_kernel<<<grid_for(n), 256, 0, st>>>(A, B, n);
+  return cudaGetLastError();
+}
+cudaError_t convert_f32_to_f64(const float *A, double *B, long n, cudaStream_t st) {
+  f32_to_f64_kernel<<<grid_for(n), 256, 0, st>>>(A, B, n);
+  return cudaGetLastError();
+}
+
+__global__ void split_scales_kernel(const double *D, int n, double *dmax_inv, double *dmin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double d = D[i];
+    dmax_inv[i] = 1.0 / fmax(d, 1.0);
+    dmin[i] = fmin(d, 1.0);
+  }
+}
+cudaError_t split_scales(const double *D, int n, double *dmax_inv, double *dmin, cudaStream_t st) {
+  split_scales_kernel<<<(n + 255) / 256, 256, 0, st>>>(D, n, dmax_inv, dmin);
+  return cudaGetLastError();
+}
+
+}  // namespace dq

@@ -1,0 +1,65 @@
+// FP64 dense linear algebra for the UDV stabilisation (row-major storage).
+#pragma once
+
+#include "common.cuh"
+
+namespace dq {
+
+// C = alpha diag(rs) op(A) op(B) diag(cs) + beta C; rs/cs may be NULL.
+// A is M x K (lda) or, transposed, K x M; B is K x N (ldb) or N x K.
+// splitk > 1 splits K over CTAs and accumulates with atomics (C is first
+// scaled by beta in a separate pass).
+cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
+                  const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
+                  const double *cs, cudaStream_t st, int splitk = 0);
+
+// Householder QR workspace for an n x n matrix: V (unit lower trapezoidal,
+// explicit), Y = V T^T and Y2 = V T per panel (panel p in columns p..p+nb),
+// tau, and the inverses of the nb x nb diagonal blocks of R.
+struct QRWork {
+  int n = 0, nb = 0;
+  double *V = nullptr, *Y = nullptr, *Y2 = nullptr, *tau = nullptr, *W = nullptr;
+  double *Rinv = nullptr;  // (n/nb + 1) blocks of nb x nb
+};
+int qr_panel_width(int n);
+size_t qr_work_doubles(int n);
+void qr_work_bind(QRWork &w, int n, double *mem);
+
+// In-place QR A = Q R (R in the upper triangle of A, V in QRWork).
+cudaError_t qr_factor(double *A, int n, QRWork &w, cudaStream_t st);
+// Q (explicit) into Qout (n x n).
+cudaError_t qr_form_q(double *Qout, int n, QRWork &w, cudaStream_t st);
+// B <- Q^T B for B n x ncols (ld ldb).
+cudaError_t qr_apply_qt(double *B, int n, int ncols, int ldb, QRWork &w, cudaStream_t st);
+// Z = R^{-1} B (R upper triangular in A's upper triangle), B destroyed; Z n x ncols.
+cudaError_t qr_solve_r(const double *A, int n, double *B, double *Z, int ncols, QRWork &w,
+                       cudaStream_t st);
+
+// ---- elementwise / small helpers
+cudaError_t set_identity(double *A, int n, int ld, cudaStream_t st);
+cudaError_t set_value(double *x, long n, double v, cudaStream_t st);
+// out[i*n + j] = in[j*ld + i] * rs[i]   (scaled transpose; rs may be NULL)
+cudaError_t transpose_scale(const double *in, int ld, double *out, int n, const double *rs,
+                            cudaStream_t st);
+// X[i, j] *= rs[i] (rs NULL skips) and *= cs[j]
+cudaError_t scale_rows_cols(double *X, int n, int ld, const double *rs, const double *cs,
+                            cudaStream_t st);
+// norms[j] = ||X[:, j]|| * D[j]
+cudaError_t column_norms_scaled(const double *X, int n, const double *D, double *norms,
+                                cudaStream_t st);
+// perm = argsort(-key) (stable, one CTA), n <= 8192
+cudaError_t argsort_desc(const double *key, int n, int *perm, cudaStream_t st);
+// out[:, c] = X[:, perm[c]] ; dP[c] = D[perm[c]] ; Trow[c, :] = T[perm[c], :]
+cudaError_t permute_udv(const double *X, const double *D, const double *T, const int *perm, int n,
+                        double *Xp, double *Dp, double *Tp, cudaStream_t st);
+// After QR of Xp: D_new[i] = |R_ii| Dp[i];  R''[i,j] = R_ij Dp[j] / D_new[i] (j >= i), 0 below.
+cudaError_t udv_diag_and_scale(double *R, int n, const double *Dp, double *Dnew, cudaStream_t st);
+// out = max |A - B| over n x n (A fp64, B float or double); result written to *out (device)
+cudaError_t max_abs_diff_f64(const double *A, const double *B, int n, double *out, cudaStream_t st);
+cudaError_t max_abs_diff_f32(const double *A, const float *B, int n, double *out, cudaStream_t st);
+cudaError_t convert_f64_to_f32(const double *A, float *B, long n, cudaStream_t st);
+cudaError_t convert_f32_to_f64(const float *A, double *B, long n, cudaStream_t st);
+// dmax = max(D, 1), dmin = min(D, 1), and their reciprocals where needed
+cudaError_t split_scales(const double *D, int n, double *dmax_inv, double *dmin, cudaStream_t st);
+
+}  // namespace dq

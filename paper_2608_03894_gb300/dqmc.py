@@ -1,0 +1,143 @@
+"""Python binding of the DQMC context API (include/dqmc.h): argument marshalling
+only; every step of the sweep runs in the CUDA library."""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import check
+
+OBS_NAMES = ("S_pair_G", "S_pair_dk", "phi2_G", "phi2_K", "density", "ekin")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching
+    allocator (on the current device and stream)."""
+
+    def __init__(self, device=None, stream=None):
+        torch = _torch()
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = stream
+
+        def _alloc(nbytes, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:  # out of memory -> NULL -> DQMC_ENOMEM
+                return None
+
+        def _free(ptr, user):
+            if ptr:
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc_cb = _lib.ALLOC_FN(_alloc)
+        self.free_cb = _lib.FREE_FN(_free)
+
+
+class DQMC:
+    """One Markov chain of the kagome attractive-Hubbard DQMC sweep.
+
+    Parameters follow the paper's notation: L (cells per side, N = 3 L^2),
+    beta, dtau (M = beta / dtau slices), U <= 0 (attraction), mu, seed.
+    Options: k (delay rank), n_stab, precision ("fp64" or "mixed"), chain,
+    timing, site_offsets, bin, drift_limit. ``use_torch`` routes device
+    memory and the stream through PyTorch."""
+
+    def __init__(self, L, beta, dtau, U, mu, seed=1, k=32, n_stab=10, precision="fp64",
+                 chain=0, timing=False, site_offsets=True, bin=10, drift_limit=1e-3,
+                 use_torch=True):
+        self.lib = _lib.load()
+        h = C.c_void_p()
+        check(self.lib.dqmc_create(int(L), float(beta), float(dtau), float(U), float(mu),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(h)))
+        self.h = h
+        self.L = int(L)
+        self.N = 3 * self.L * self.L
+        self.M = int(round(beta / dtau))
+        self._alloc = None
+        prec = {"fp64": 0, "mixed": 1, 0: 0, 1: 1}[precision]
+        opts = dict(k=k, n_stab=n_stab, precision=prec, chain=chain, timing=int(bool(timing)),
+                    site_offsets=int(bool(site_offsets)), bin=bin, drift_limit=drift_limit)
+        for key, v in opts.items():
+            self.set_option(key, v)
+        if use_torch:
+            torch = _torch()
+            if torch.cuda.is_available():
+                self._alloc = TorchAllocator()
+                check(self.lib.dqmc_set_allocator(self.h, self._alloc.alloc_cb, self._alloc.free_cb, None))
+                self.set_stream(torch.cuda.current_stream().cuda_stream)
+
+    # -- options / plumbing
+    def set_option(self, key, value):
+        check(self.lib.dqmc_set_option(self.h, key.encode(), float(value)))
+
+    def set_stream(self, stream_handle):
+        check(self.lib.dqmc_set_stream(self.h, C.c_void_p(int(stream_handle))))
+
+    # -- the hot path
+    def sweep(self, n=1, measure=False):
+        check(self.lib.dqmc_sweep(self.h, int(n), int(bool(measure))))
+
+    def green(self, slice_index=0):
+        G = np.empty((self.N, self.N), dtype=np.float64)
+        check(self.lib.dqmc_green(self.h, int(slice_index), G.ctypes.data_as(C.c_void_p)))
+        return G
+
+    def running_green(self):
+        G = np.empty((self.N, self.N), dtype=np.float64)
+        sl = C.c_int(0)
+        check(self.lib.dqmc_get_running_green(self.h, G.ctypes.data_as(C.c_void_p), C.byref(sl)))
+        return G, sl.value
+
+    def measure(self):
+        o = _lib.Obs()
+        check(self.lib.dqmc_measure(self.h, C.byref(o)))
+        out = {n: getattr(o, n) for n in OBS_NAMES}
+        out["err"] = dict(zip(OBS_NAMES, list(o.err)))
+        for n in ("n_samples", "n_bins", "R_pair", "R_pair_err", "P", "P_err", "D_G", "D_K"):
+            out[n] = getattr(o, n)
+        return out
+
+    def stats(self):
+        s = _lib.Stats()
+        check(self.lib.dqmc_get_stats(self.h, C.byref(s)))
+        return {n: getattr(s, n) for n, _ in _lib.Stats._fields_}
+
+    @property
+    def field(self):
+        f = np.empty((self.M, self.N), dtype=np.int8)
+        check(self.lib.dqmc_get_field(self.h, f.ctypes.data_as(C.c_void_p)))
+        return f
+
+    @field.setter
+    def field(self, value):
+        f = np.ascontiguousarray(np.asarray(value, dtype=np.int8).reshape(self.M, self.N))
+        check(self.lib.dqmc_set_field(self.h, f.ctypes.data_as(C.c_void_p)))
+
+    def save(self, path):
+        check(self.lib.dqmc_save(self.h, str(path).encode()))
+
+    def load(self, path):
+        check(self.lib.dqmc_load(self.h, str(path).encode()))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.dqmc_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU,
+exports every function include/dqmc.h declares, and validates arguments
+before touching the device."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2608_03894_gb300 import _build
+    _build.build()
+    from paper_2608_03894_gb300 import _lib
+    return _lib.load()
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "dqmc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dqmc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for required in ("dqmc_create", "dqmc_sweep", "dqmc_green", "dqmc_measure", "dqmc_destroy",
+                     "dqmc_op_propagate_f64", "dqmc_op_flush_f32", "dqmc_op_metropolis_block"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2608_03894_gb300 import _lib
+    assert set(header_functions()) == set(_lib.SIGNATURES)
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.dqmc_version()
+
+
+def _create(lib, L=4, beta=2.0, dtau=0.1, U=-4.0, mu=-1.0, seed=1):
+    h = C.c_void_p()
+    st = lib.dqmc_create(L, beta, dtau, U, mu, seed, C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("args,why", [
+    (dict(U=4.0), "U"), (dict(L=5), "unsupported L"), (dict(L=0), "unsupported L"),
+    (dict(beta=1.05), "integer"), (dict(dtau=0.0), "positive"), (dict(mu=float("nan")), "finite"),
+])
+def test_create_rejects_bad_parameters(lib, args, why):
+    st, h = _create(lib, **args)
+    assert st == 1  # DQMC_EINVAL
+    assert why in lib.dqmc_last_error().decode()
+    assert not h.value
+
+
+def test_create_and_destroy_without_gpu_work(lib):
+    st, h = _create(lib)
+    assert st == 0 and h.value
+    assert lib.dqmc_set_option(h, b"k", 16.0) == 0
+    assert lib.dqmc_set_option(h, b"k", 7.0) == 1
+    assert lib.dqmc_set_option(h, b"precision", 2.0) == 1
+    assert lib.dqmc_set_option(h, b"nonsense", 1.0) == 1
+    assert lib.dqmc_set_option(h, b"n_stab", 0.0) == 1
+    assert lib.dqmc_set_option(h, b"drift_limit", -1.0) == 1
+    assert lib.dqmc_set_option(h, None, 1.0) == 1
+    lib.dqmc_destroy(h)
+
+
+def test_null_arguments(lib):
+    assert lib.dqmc_create(4, 2.0, 0.1, -4.0, -1.0, 1, None) == 1
+    assert lib.dqmc_sweep(None, 1, 0) == 1
+    st, h = _create(lib)
+    assert lib.dqmc_sweep(h, -1, 0) == 1
+    assert lib.dqmc_green(h, 0, None) == 1
+    assert lib.dqmc_green(h, 999, C.c_void_p(1)) == 1   # slice out of range, checked first
+    lib.dqmc_destroy(h)
+
+
+def test_operator_argument_validation(lib):
+    # rejected on the host before any launch
+    assert lib.dqmc_op_propagate_f64(5, -0.1, 0, C.c_void_p(16), C.c_void_p(16), 1, 1, None, None, None, None) == 1
+    assert lib.dqmc_op_propagate_f64(4, -0.1, 2, C.c_void_p(16), C.c_void_p(16), 1, 1, None, None, None, None) == 1
+    assert lib.dqmc_op_propagate_f64(4, -0.1, 1, C.c_void_p(16), C.c_void_p(16), 1, 10, None, None, None, None) == 1
+    assert lib.dqmc_op_flush_f64(48, 40, 16, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), None) == 1
+    assert lib.dqmc_op_metropolis_block(48, 0, 65, C.c_void_p(16), 65, C.c_void_p(16), 0.5, 1, 0, 0, 1,
+                                        None, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), None) == 1

@@ -1,0 +1,268 @@
+"""GPU parity of every hot-path step against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: FP64 kernels 1e-12 (single steps) and 1e-10 (whole sweeps /
+from-scratch G), the bar the FP64 path is held to; FP32 propagation 2e-6
+relative to max|Y| (a few FP32 roundings through log2(L^2) butterfly stages);
+mixed-precision sweeps max |G_wrapped - G_fresh| <= 1e-6.
+"""
+
+import numpy as np
+import pytest
+
+from dqmc_inputs import random_field, random_green_like, random_matrix
+from oracle import dqmc as odqmc
+from oracle import green as ogreen
+from oracle import lattice as olat
+from oracle import measure as omeas
+from oracle import model as omodel
+from oracle import philox as ophilox
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_03894_gb300 as p
+    return p
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+# ------------------------------------------------------------------ Eq. 5-6 propagation
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 6, 8, 12, 16, 24, 36])
+@pytest.mark.parametrize("side", [0, 1])
+def test_propagate_f64_matches_dense_exponential(pkg, L, side):
+    N = 3 * L * L
+    nvec = 37 if L > 2 else 5          # ragged against every tile width
+    scale = -0.1 if side == 0 else 0.1
+    X = random_matrix(N, nvec, seed=L) if side == 0 else random_matrix(nvec, N, seed=L)
+    rng = np.random.default_rng(100 + L)
+    pre, post = rng.uniform(0.5, 2.0, N), rng.uniform(0.5, 2.0, N)
+    vs = rng.uniform(0.5, 2.0, nvec)
+    E = olat.expm_hermitian(olat.kinetic_matrix(L), scale)
+    if side == 0:
+        ref = (post[:, None] * (E @ (pre[:, None] * X))) * vs[None, :]
+    else:
+        ref = vs[:, None] * (((X * pre[None, :]) @ E) * post[None, :])
+    Y = pkg.ops.propagate(L, scale, side, dev(X), pre=dev(pre), post=dev(post), vscale=dev(vs))
+    err = np.max(np.abs(Y.cpu().numpy() - ref))
+    assert err < 1e-12 * max(1.0, np.max(np.abs(ref))), err
+
+
+@pytest.mark.parametrize("L", [4, 12, 24, 36])
+def test_propagate_f32(pkg, L):
+    N = 3 * L * L
+    X = random_matrix(N, 40, seed=7)
+    E = olat.expm_hermitian(olat.kinetic_matrix(L), -0.1)
+    ref = E @ X
+    Y = pkg.ops.propagate(L, -0.1, 0, dev(X, torch.float32))
+    err = np.max(np.abs(Y.double().cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < 2e-6, err
+    Xr = X.T.copy()
+    Yr = pkg.ops.propagate(L, -0.1, 1, dev(Xr, torch.float32))
+    err = np.max(np.abs(Yr.double().cpu().numpy() - Xr @ E)) / np.max(np.abs(ref))
+    assert err < 2e-6, err
+
+
+def test_propagate_in_place_and_identity(pkg):
+    L = 6
+    N = 3 * L * L
+    X = dev(random_matrix(N, N, seed=3))
+    Xc = X.clone()
+    pkg.ops.propagate(L, -0.1, 0, X, Y=X)          # in place
+    pkg.ops.propagate(L, 0.1, 0, X, Y=X)           # inverse
+    assert torch.max(torch.abs(X - Xc)).item() < 1e-12
+    Y = pkg.ops.propagate(L, 0.0, 1, Xc)           # e^{0} = I
+    assert torch.max(torch.abs(Y - Xc)).item() < 1e-13
+
+
+# ------------------------------------------------------------------ delayed update
+def _oracle_slice_update(L, beta, U, G0, field, l, pas, seed, sweep):
+    ch = odqmc.Chain(L, beta, 0.1, U, -1.0, seed=seed, n_stab=1000)
+    ch.field = field.copy()
+    ch.G = G0.copy()
+    ch.sweeps_done = sweep
+    ch.update_slice(l, pas)
+    return ch.G, ch.field
+
+
+@pytest.mark.parametrize("L,k", [(2, 4), (4, 8), (4, 32), (6, 64), (6, 16)])
+def test_delayed_update_slice_matches_one_at_a_time(pkg, L, k):
+    """A whole slice of proposals by blocks of k (Metropolis block + rank-k
+    flush) reproduces the oracle's one-at-a-time Sherman-Morrison sweep: same
+    decisions from the same Philox stream, same G."""
+    beta, U, seed, sweep, l, pas = 0.5, -4.0, 5, 3, 2, 1
+    m = omodel.Model(L, beta, 0.1, U, -1.0)
+    N = m.N
+    field = random_field(m.M, N, seed=L)
+    G0 = ogreen.green_direct(m, field, l)
+    Gref, fref = _oracle_slice_update(L, beta, U, G0, field, l, pas, seed, sweep)
+
+    G = dev(G0)
+    s = dev(field[l - 1], torch.int8)
+    for s0 in range(0, N, k):
+        kb = min(k, N - s0)
+        Gcol = G[:, s0:s0 + kb].contiguous()
+        Grow = G[s0:s0 + kb, :].contiguous()
+        g = G[s0:s0 + kb, s0:s0 + kb].contiguous()
+        Gam, nacc, st = pkg.ops.metropolis_block(N, s0, kb, g, s, m.lam, seed, 0, 2 * sweep + pas, l)
+        assert st == 0
+        pkg.ops.flush(N, s0, kb, G, Gcol, Grow, Gam)
+    assert np.array_equal(s.cpu().numpy(), fref[l - 1])
+    assert np.max(np.abs(G.cpu().numpy() - Gref)) < 1e-12
+
+
+def test_forced_flips_and_fp32_flush(pkg):
+    L, k = 4, 16
+    m = omodel.Model(L, 0.5, 0.1, -4.0, -1.0)
+    N = m.N
+    field = random_field(m.M, N, seed=9)
+    G0 = ogreen.green_direct(m, field, 1)
+    forced = np.zeros(N, dtype=bool)
+    forced[[0, 3, 5, 17, 18, 40, 47]] = True
+    ch = odqmc.Chain(L, 0.5, 0.1, -4.0, -1.0, seed=1)
+    ch.field, ch.G = field.copy(), G0.copy()
+    ch.update_slice(1, 0, forced)
+    G = dev(G0)
+    G32 = dev(G0, torch.float32)
+    s = dev(field[0], torch.int8)
+    s32 = s.clone()
+    for s0 in range(0, N, k):
+        f = dev(forced[s0:s0 + k], torch.uint8)
+        Gam, _, _ = pkg.ops.metropolis_block(N, s0, k, G[s0:s0 + k, s0:s0 + k].contiguous(), s, m.lam,
+                                             1, 0, 0, 1, forced=f)
+        pkg.ops.flush(N, s0, k, G, G[:, s0:s0 + k].contiguous(), G[s0:s0 + k, :].contiguous(), Gam)
+        g32 = G32[s0:s0 + k, s0:s0 + k].double().contiguous()
+        Gam32, _, _ = pkg.ops.metropolis_block(N, s0, k, g32, s32, m.lam, 1, 0, 0, 1, forced=f)
+        pkg.ops.flush(N, s0, k, G32, G32[:, s0:s0 + k].contiguous(), G32[s0:s0 + k, :].contiguous(), Gam32)
+    assert np.array_equal(s.cpu().numpy(), ch.field[0])
+    assert np.max(np.abs(G.cpu().numpy() - ch.G)) < 1e-12
+    assert np.max(np.abs(G32.double().cpu().numpy() - ch.G)) < 1e-5
+
+
+# ------------------------------------------------------------------ measurement
+@pytest.mark.parametrize("L,offsets", [(4, True), (6, True), (12, True), (12, False)])
+def test_measure_matches_wick_estimators(pkg, L, offsets):
+    N = 3 * L * L
+    G = random_green_like(N, seed=L)
+    obs = omeas.Observables(L, L, olat.kinetic_matrix(L), site_offsets=offsets)(G)
+    got = pkg.ops.measure(L, dev(G), site_offsets=offsets)
+    for key, v in obs.items():
+        if np.isnan(v):
+            assert np.isnan(got[key])
+        else:
+            assert abs(got[key] - v) < 1e-12 * max(1.0, abs(v)), key
+
+
+# ------------------------------------------------------------------ whole context
+def test_green_from_scratch_fixed_field_L4(pkg):
+    par = dict(L=4, beta=2.0, dtau=0.1, U=-4.0, mu=-1.0)
+    m = omodel.Model(**par)
+    f = random_field(m.M, m.N, seed=1)
+    with pkg.DQMC(**par, seed=1, k=8, n_stab=10) as d:
+        d.field = f
+        for l in (0, 7, 10, 20):
+            assert np.max(np.abs(d.green(l) - ogreen.green_udv(m, f, l))) < 1e-10
+
+
+def test_green_from_scratch_fixed_field_L12(pkg):
+    par = dict(L=12, beta=12.0, dtau=0.1, U=-4.0, mu=-1.0)
+    m = omodel.Model(**par)
+    f = random_field(m.M, m.N, seed=1)
+    with pkg.DQMC(**par, seed=1, k=32, n_stab=10) as d:
+        d.field = f
+        for l in (0, 50):
+            assert np.max(np.abs(d.green(l) - ogreen.green_udv(m, f, l))) < 1e-10
+
+
+def test_u0_closed_form_on_gpu(pkg):
+    par = dict(L=12, beta=12.0, dtau=0.1, U=0.0, mu=-1.0)
+    m = omodel.Model(**par)
+    with pkg.DQMC(**par, seed=3, k=32, n_stab=10) as d:
+        assert np.max(np.abs(d.green(0) - m.green_free())) < 1e-10
+        d.sweep(1)
+        G, sl = d.running_green()
+        assert sl == 0
+        assert np.max(np.abs(G - m.green_free())) < 1e-10
+
+
+@pytest.mark.parametrize("L,k,n_stab,beta", [(4, 8, 10, 2.0), (6, 16, 5, 1.0), (2, 4, 3, 0.7)])
+def test_identical_field_history_20_sweeps(pkg, L, k, n_stab, beta):
+    """Fed the same Philox stream, the GPU chain makes exactly the oracle's
+    decisions for 20 sweeps (fields bit-identical after every sweep) and its G
+    stays within 1e-10."""
+    par = dict(L=L, beta=beta, dtau=0.1, U=-4.0, mu=-1.0)
+    ref = odqmc.Chain(**par, seed=1, n_stab=n_stab)
+    with pkg.DQMC(**par, seed=1, k=k, n_stab=n_stab) as d:
+        assert np.array_equal(d.field, ref.field)
+        for s in range(20):
+            d.sweep(1)
+            ref.sweep()
+            assert np.array_equal(d.field, ref.field), f"sweep {s}"
+        G, _ = d.running_green()
+        assert np.max(np.abs(G - ref.G)) < 1e-10
+        st = d.stats()
+        assert st["accepted"] == ref.accepted and st["proposed"] == ref.proposed
+
+
+def test_measurements_equal_oracle_samples(pkg):
+    par = dict(L=4, beta=1.0, dtau=0.1, U=-4.0, mu=-1.0)
+    ref = odqmc.Chain(**par, seed=2, n_stab=5)
+    with pkg.DQMC(**par, seed=2, k=8, n_stab=5, bin=5) as d:
+        d.sweep(10, measure=True)
+        ref.run(10, measure_obs=True)
+        got = d.measure()
+        assert got["n_samples"] == len(ref.samples)
+        for key in ("S_pair_G", "S_pair_dk", "phi2_G", "density", "ekin"):
+            want = np.mean([smp[key] for smp in ref.samples])
+            assert abs(got[key] - want) < 1e-10, key
+
+
+def test_mixed_precision_drift_L12(pkg):
+    par = dict(L=12, beta=12.0, dtau=0.1, U=-4.0, mu=-1.0)
+    with pkg.DQMC(**par, seed=1, k=32, n_stab=10, precision="mixed") as d:
+        d.sweep(2)
+        st = d.stats()
+        assert 0 < st["max_drift"] <= 1e-6, st["max_drift"]
+        m = omodel.Model(**par)
+        G, sl = d.running_green()
+        Gf = ogreen.green_udv(m, d.field, sl)
+        assert np.max(np.abs(G - Gf)) <= 1e-6
+
+
+def test_checkpoint_resume_is_exact(pkg, tmp_path):
+    par = dict(L=4, beta=1.0, dtau=0.1, U=-4.0, mu=-1.0)
+    with pkg.DQMC(**par, seed=4, k=8, n_stab=5) as a:
+        a.sweep(3)
+        a.save(tmp_path / "ck.bin")
+        a.sweep(3)
+        fa = a.field
+    with pkg.DQMC(**par, seed=99, k=8, n_stab=5) as b:
+        b.load(tmp_path / "ck.bin")
+        b.sweep(3)
+        assert np.array_equal(b.field, fa)
+
+
+def test_allocator_failure_reports_enomem(pkg):
+    import ctypes as C
+    from paper_2608_03894_gb300 import _lib
+    lib = _lib.load()
+    h = C.c_void_p()
+    assert lib.dqmc_create(4, 1.0, 0.1, -4.0, -1.0, 1, C.byref(h)) == 0
+    calls = []
+
+    def bad_alloc(n, u):
+        calls.append(n)
+        return None
+
+    a_cb, f_cb = _lib.ALLOC_FN(bad_alloc), _lib.FREE_FN(lambda p, u: None)
+    assert lib.dqmc_set_allocator(h, a_cb, f_cb, None) == 0
+    assert lib.dqmc_sweep(h, 1, 0) == 2  # DQMC_ENOMEM
+    assert calls
+    lib.dqmc_destroy(h)
