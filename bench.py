@@ -1,0 +1,338 @@
+"""Benchmark: site-updates/s of the kagome DQMC sweep on GB300.
+
+One step = one sweep (up + down pass, 2 N M Metropolis proposals) of one
+Markov chain per GPU, on synthetic input (Philox-initialised Ising field).
+Default workload: L = 24 (N = 1728), beta = 24, dtau = 0.1 (M = 240), U = -4
+(|U| = 4 attractive), mu = -1, delay rank k = 32, stabilisation every 8
+slices, mixed precision.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+               [--workload NAME] [--precision fp64|mixed|fp32]
+Under torchrun every rank runs its own chain (seed + rank): replicas, weak
+scaling, no data-path collective. Rank 0 prints one JSON line.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from dqmc_inputs import WORKLOADS  # noqa: E402
+
+METRIC = "site-updates/s per GB300 at L=24 kagome: FP32+FP64-stab vs plain FP64 at |ΔG|≤1e-6"
+UNIT = "site-updates/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# GB300: 152 SMs; per SM per clock 128 FP32 FMA and 2 FP64 FMA (the FP64 rate
+# is 1/64 of FP32 on this part: 152 * 2 * 2 * 2.07 GHz = 1.26 TFLOP/s, the
+# nominal 1.25 TFLOP/s)
+N_SM = 152
+
+
+def alu_peak_tflops(kind, mhz):
+    per_sm_flops = {"fp64": 2 * 2, "fp32": 128 * 2}[kind]
+    return N_SM * per_sm_flops * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ("active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for _, _, flags in rows:
+            for n, v in zip(names[1:], flags[1:]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def workload(args):
+    w = dict(WORKLOADS[args.workload])
+    if args.precision:
+        w["precision"] = args.precision
+    return w
+
+
+def config_dict(w, world):
+    L = w["L"]
+    M = int(round(w["beta"] / w["dtau"]))
+    return {
+        "workload": f"{args_global.workload}: kagome L={L} (N={3 * L * L}), beta={w['beta']}, dtau={w['dtau']} "
+                    f"(M={M}), U={w['U']}, mu={w['mu']}, k={w['k']}, n_stab={w['n_stab']}, "
+                    f"precision={w['precision']}, one chain per GPU",
+        "L": L, "N": 3 * L * L, "M": M, "beta": w["beta"], "U": w["U"], "mu": w["mu"], "k": w["k"],
+        "n_stab": w["n_stab"], "precision": w["precision"], "parallelism": f"replicas x{world}",
+        "l2": "working set larger than L2 (UDV stacks and G per chain)",
+    }
+
+
+def cpu_oracle_sample(w, budget_s=20.0):
+    """The oracle as it stands on this host: wrap + N proposals per slice visit
+    (refresh excluded), the number of visits sized to ~budget_s."""
+    from oracle import dqmc as odqmc
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    t1, n1, _ = odqmc.time_slice_visits(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], w["seed"], 1,
+                                        n_stab=w["n_stab"], with_refresh=False)
+    visits = max(1, min(64, int(budget_s / max(t1, 1e-3))))
+    t, n, _ = odqmc.time_slice_visits(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], w["seed"], visits,
+                                      n_stab=w["n_stab"], with_refresh=False)
+    return {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{visits} up-pass slice visits at L={w['L']} (wrap + {3 * w['L'] ** 2} one-at-a-time "
+                      f"proposals each, numpy FP64 on {cores} host threads), UDV refresh excluded, {t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    w = workload(args)
+    if rank != 0:
+        return
+    per_step = []
+    samples = None
+    for i in range(args.warmup + args.steps):
+        s = cpu_oracle_sample(w, budget_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            per_step.append(s)
+        samples = s
+    value = statistics.mean(s["value"] for s in per_step)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * 2 * (3 * w["L"] ** 2) * int(round(w["beta"] / w["dtau"])) / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Philox-initialised Ising field)", "config": config_dict(w, world),
+        "cpu_baseline": {k: samples[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    import paper_2608_03894_gb300 as pkg
+    from paper_2608_03894_gb300 import _lib
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    w = workload(args)
+    L, N = w["L"], 3 * w["L"] ** 2
+    M = int(round(w["beta"] / w["dtau"]))
+    units_per_step = 2 * N * M
+    d = pkg.DQMC(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], seed=w["seed"] + rank, k=w["k"],
+                 n_stab=w["n_stab"], precision=w["precision"], chain=rank)
+    stream = torch.cuda.current_stream()
+    d.sweep(args.warmup)
+    launches0 = d.stats()["launches"]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- timed region: K sweeps, device time on the library's stream
+    sampler = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    with sampler:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        d.sweep(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = d.stats()
+    launches = st["launches"] - launches0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units_per_step * args.steps * world / (ms / 1000.0)
+    clocks = sampler.summary()
+
+    # ---- end to end through the public API: field in from pinned host memory,
+    # one sweep with measurements, field and observables back to the host
+    e2e = None
+    if not args.no_e2e:
+        lib = _lib.load()
+        fin = torch.empty((M, N), dtype=torch.int8, pin_memory=True)
+        fout = torch.empty((M, N), dtype=torch.int8, pin_memory=True)
+        fin.numpy()[:] = d.field
+        obs = _lib.Obs()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _lib.check(lib.dqmc_set_field(d.h, C.c_void_p(fin.data_ptr())))
+            _lib.check(lib.dqmc_sweep(d.h, 1, 1))
+            _lib.check(lib.dqmc_get_field(d.h, C.c_void_p(fout.data_ptr())))
+            _lib.check(lib.dqmc_measure(d.h, C.byref(obs)))
+            fin.copy_(fout)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": units_per_step * args.steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": M * N, "d2h_bytes_per_step": M * N + 6 * 8 * (-(-M // w["n_stab"]))}
+
+    # ---- one extra sweep with per-kernel-family CUDA events for the roofline
+    d.set_option("timing", 2)
+    s0 = d.stats()
+    d.sweep(1)
+    s1 = d.stats()
+    d.set_option("timing", 0)
+    fam = {}
+    for f in s1["ms_kernel"]:
+        dt = s1["ms_kernel"][f] - s0["ms_kernel"][f]
+        n = s1["n_kernel"][f] - s0["n_kernel"][f]
+        fam[f] = {"ms": dt, "launches": n, "flops": s1["flops_kernel"][f] - s0["flops_kernel"][f],
+                  "bytes": s1["bytes_kernel"][f] - s0["bytes_kernel"][f]}
+    total_ms = sum(v["ms"] for v in fam.values())
+    dom = max(fam, key=lambda f: fam[f]["ms"])
+    peaks, peak_src = load_peaks()
+    mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fd = fam[dom]
+    per_launch_s = fd["ms"] / 1000.0 / max(1, fd["launches"])
+    if dom == "prop":
+        achieved = fd["bytes"] / max(1, fd["launches"]) / per_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"{peak_src} copy bandwidth"}
+    else:
+        kind = "fp64" if (w["precision"] == "fp64" or dom in ("qr_panel",)) else "fp32"
+        if dom == "gemm" and w["precision"] == "fp64":
+            kind = "fp64"
+        achieved = fd["flops"] / max(1, fd["launches"]) / per_launch_s / 1e12
+        peak = alu_peak_tflops(kind, peaks.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"{kind} issue rate x 152 SMs x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    roof["share_of_device_time"] = fd["ms"] / max(total_ms, 1e-9)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_sample(w, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "mixed": "f64-accurate (f32-pair) bulk + f64", "fp32": "f32 + f64 stab"}[w["precision"]],
+            "data": "synthetic (Philox-initialised Ising field, seed 1 + rank)",
+            "config": config_dict(w, world),
+            "max_drift": st["max_drift"],
+            "acceptance": st["accepted"] / max(1, st["proposed"]),
+            "sweeps_per_s": args.steps * world / (ms / 1000.0),
+            "phase_breakdown_ms": {f: round(v["ms"], 3) for f, v in fam.items()},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    d.close()
+
+
+def main():
+    global args_global
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="L24_mixed", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=("fp64", "mixed", "fp32"))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    args_global = args
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+args_global = None
+
+if __name__ == "__main__":
+    main()

@@ -78,7 +78,17 @@ typedef struct {
   long accepted;
   double max_drift;      /* max |G_wrapped - G_fresh| at stabilisation points */
   double last_drift;     /* same, over the last sweep only */
-  double ms_wrap, ms_update, ms_stab, ms_measure; /* device time per phase (when timing is on) */
+  double ms_wrap, ms_update, ms_stab, ms_measure; /* device time per phase (timing >= 1) */
+  /* device time and launch count per kernel family (timing = 2): 0 FFT
+   * propagation, 1 Metropolis block, 2 rank-k flush, 3 GEMM, 4 QR panel,
+   * 5 measurement, 6 other */
+  double ms_kernel[7];
+  long n_kernel[7];
+  /* algorithmic work per family (any timing): flops of the operation and
+   * bytes of one read of its inputs plus one write of its outputs */
+  double flops_kernel[7];
+  double bytes_kernel[7];
+  unsigned long long launches; /* kernel launches issued for this context (any timing) */
 } dqmc_stats;
 
 /* ------------------------------------------------------------------ context API */
@@ -96,7 +106,8 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
 /* Options (numbers): "k" delay rank (1..64, default 32), "n_stab" slices between
  * UDV refreshes (default 10), "precision" (0 = plain FP64, 1 = FP32 propagation
  * and flush with FP64 stabilisation and ratios), "chain" (Philox chain id),
- * "timing" (1 = per-phase CUDA-event timers), "site_offsets" (1 = S_Pair phases
+ * "timing" (1 = per-phase CUDA-event timers, 2 = also per kernel family; the
+ * events themselves cost time, so time throughput with 0), "site_offsets" (1 = S_Pair phases
  * use site positions R + tau_a, 0 = cell positions), "bin" (measurements per
  * bin, default 10), "drift_limit" (hard limit, default 1e-3 -> DQMC_ENUMERIC).
  * "k", "n_stab", "precision" and "chain" are accepted only before the first

@@ -161,19 +161,33 @@ class Chain:
         return x[:nb * bin_size].reshape(nb, bin_size, len(keys)).mean(axis=1)
 
 
-def time_slice_visits(L, beta, dtau, U, mu, seed, n_visits, n_stab=8):
-    """Wall time of ``n_visits`` up-pass slice visits (wrap + N proposals, with
-    the stack refresh at checkpoints) after start-up; returns (seconds,
-    proposals, number of refreshes). Used for the CPU baseline."""
-    ch = Chain(L, beta, dtau, U, mu, seed, n_stab=n_stab)
+def time_slice_visits(L, beta, dtau, U, mu, seed, n_visits, n_stab=8, with_refresh=True):
+    """Wall time of ``n_visits`` up-pass slice visits (wrap + N proposals, and
+    with_refresh: the stack update and refresh at checkpoints) after start-up;
+    returns (seconds, proposals, number of refreshes). Used for the CPU
+    baseline. Without refresh the chain starts from the U = 0 closed-form G
+    (no start-up stack build, which at L = 24 alone takes minutes)."""
+    ch = Chain.__new__(Chain)
+    ch.model = Model(L, beta, dtau, U, mu)
     m = ch.model
+    ch.N, ch.M, ch.seed, ch.chain, ch.n_stab = m.N, m.M, int(seed), 0, int(n_stab)
+    ch.C = -(-ch.M // ch.n_stab)
+    ch.tau = [min(c * ch.n_stab, ch.M) for c in range(ch.C + 1)]
+    ch.field = philox.initial_field(seed, 0, ch.M, ch.N)
+    ch.sweeps_done, ch.max_drift, ch.accepted, ch.proposed = 0, 0.0, 0, 0
+    ch._e2ls = {1: math.exp(2 * m.lam), -1: math.exp(-2 * m.lam)}
+    ch._delta = {1: math.exp(-2 * m.lam) - 1.0, -1: math.exp(2 * m.lam) - 1.0}
+    if with_refresh:
+        ch.reset_green()
+    else:
+        ch.G = m.green_free()
     t0 = time.perf_counter()
     c = 1
     refreshes = 0
     for l in range(1, n_visits + 1):
         ch.G = m.B(ch.field[l - 1]) @ ch.G @ m.Binv(ch.field[l - 1])
         ch.update_slice(l, 0)
-        if l == ch.tau[c]:
+        if with_refresh and l == ch.tau[c]:
             ch.right[c] = ch._chunk_right(ch.right[c - 1].copy(), c)
             ch._refresh(c)
             refreshes += 1

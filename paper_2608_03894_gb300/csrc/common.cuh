@@ -78,4 +78,40 @@ constexpr uint32_t kDomainInit = 1u;
 // ------------------------------------------------------------------ launch helpers
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Kernel families for per-family device timing (dqmc_stats.ms_kernel).
+enum KFam { KF_PROP = 0, KF_METRO, KF_FLUSH, KF_GEMM, KF_QRPANEL, KF_MEASURE, KF_OTHER, KF_COUNT };
+
+// Optional per-launch event recorder, installed by the engine for the calling
+// thread while a context runs with per-kernel timing; every launch site wraps
+// its launch in a KScope, which also counts launches.
+struct KTimerSink {
+  virtual void begin(int fam, cudaStream_t st) = 0;
+  virtual void end(int fam, cudaStream_t st) = 0;
+  virtual ~KTimerSink() {}
+};
+KTimerSink *&ktimer_sink();
+void count_launch();
+unsigned long long launch_count();
+// Algorithmic work of the launches issued by the calling thread, per family
+// (flops of the mathematical operation, bytes of one read of every input and
+// one write of every output); read by the engine for the roofline figures.
+void add_work(int fam, double flops, double bytes);
+const double *work_flops();
+const double *work_bytes();
+
+struct KScope {
+  int fam;
+  cudaStream_t st;
+  KScope(int f, cudaStream_t s) : fam(f), st(s) {
+    if (ktimer_sink()) ktimer_sink()->begin(f, s);
+  }
+  ~KScope() {
+    count_launch();
+    if (ktimer_sink()) ktimer_sink()->end(fam, st);
+  }
+};
+#define DQ_KSCOPE_CAT2(a, b) a##b
+#define DQ_KSCOPE_CAT(a, b) DQ_KSCOPE_CAT2(a, b)
+#define DQ_KSCOPE(fam, st) ::dq::KScope DQ_KSCOPE_CAT(dq_kscope_, __LINE__)(fam, st)
+
 }  // namespace dq

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -37,6 +38,21 @@ dqmc_status fail(dqmc_status st, const std::string &msg) {
 dqmc_status cuda_fail(cudaError_t e, const char *what) {
   return fail(DQMC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// ---------------------------------------------------------------- launch accounting
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local KTimerSink *t_sink = nullptr;
+KTimerSink *&ktimer_sink() { return t_sink; }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+static thread_local double t_flops[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+static thread_local double t_bytes[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+void add_work(int fam, double flops, double bytes) {
+  t_flops[fam] += flops;
+  t_bytes[fam] += bytes;
+}
+const double *work_flops() { return t_flops; }
+const double *work_bytes() { return t_bytes; }
 
 // ---------------------------------------------------------------- shared-memory opt-in
 // cudaFuncSetAttribute is per device; remember (function, device) pairs.
@@ -180,12 +196,19 @@ struct dqmc_ctx {
   double *ph_pc = nullptr, *ph_ps = nullptr, *ph_wgc = nullptr, *ph_wgs = nullptr,
          *ph_wkc = nullptr, *ph_wks = nullptr;
   int *nbr = nullptr;
+  float2 *dfws = nullptr;  // double-float GEMM workspace (mixed precision)
+  size_t dfws_elems = 0;
   bool haveK = false;
   // host statistics
   long sweeps = 0, proposed = 0, accepted = 0;
   double max_drift = 0.0, last_drift = 0.0;
   std::vector<std::array<double, 6>> samples;
   double ms_wrap = 0, ms_update = 0, ms_stab = 0, ms_measure = 0;
+  double ms_kernel[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  long n_kernel[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  double flops_kernel[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  double bytes_kernel[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  unsigned long long launches = 0;
 };
 
 namespace {
@@ -237,7 +260,7 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
   DQ_CHECK(ctx_alloc_n(c, &c->field, (size_t)M * N));
   DQ_CHECK(ctx_alloc_n(c, &c->G64, NN));
   DQ_CHECK(ctx_alloc_n(c, &c->Gf, NN));
-  if (c->precision == 1) DQ_CHECK(ctx_alloc_n(c, &c->G32, NN));
+  if (c->precision == 2) DQ_CHECK(ctx_alloc_n(c, &c->G32, NN));
   c->right.resize(c->C + 1);
   c->left.resize(c->C + 1);
   for (int q = 0; q <= c->C; ++q) {
@@ -273,7 +296,12 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
   DQ_CHECK(ctx_alloc_n(c, &c->evi64, (size_t)N));
   DQ_CHECK(ctx_alloc_n(c, &c->ev32, (size_t)N));
   DQ_CHECK(ctx_alloc_n(c, &c->evi32, (size_t)N));
-  const size_t es = c->precision == 1 ? sizeof(float) : sizeof(double);
+  if (c->precision == 1) {
+    // split operands of the double-float GEMMs: at most M*K + K*N = 2 N^2 pairs
+    c->dfws_elems = 2 * NN;
+    DQ_CHECK(ctx_alloc_n(c, &c->dfws, c->dfws_elems));
+  }
+  const size_t es = c->precision == 2 ? sizeof(float) : sizeof(double);
   for (int b = 0; b < 2; ++b) {
     DQ_CHECK(ctx_alloc(c, &c->Gcol[b], (size_t)N * c->k * es));
     DQ_CHECK(ctx_alloc(c, &c->Grow[b], (size_t)N * c->k * es));
@@ -359,6 +387,7 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
   // initial field
   const uint32_t k0 = (uint32_t)(c->seed & 0xffffffffu), k1 = (uint32_t)(c->seed >> 32);
   const uint32_t c3 = ((uint32_t)c->chain & 0xffffffu) | (kDomainInit << 24);
+  DQ_KSCOPE(KF_OTHER, c->stream);
   init_field_kernel<<<256, 256, 0, c->stream>>>(c->field, M, N, k0, k1, c3);
   CK(cudaGetLastError());
   c->allocated = true;
@@ -368,6 +397,7 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
 // ---------------------------------------------------------------- propagation helpers
 dqmc_status compute_expv(dqmc_ctx *c, int l) {
   const double vp = std::exp(c->lam + c->dtau * c->mu), vm = std::exp(-c->lam + c->dtau * c->mu);
+  DQ_KSCOPE(KF_OTHER, c->stream);
   expv_kernel<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->field + (size_t)(l - 1) * c->N, c->N,
                                                          vp, vm, c->ev64, c->evi64, c->ev32,
                                                          c->evi32);
@@ -379,7 +409,7 @@ dqmc_status compute_expv(dqmc_ctx *c, int l) {
 dqmc_status wrap(dqmc_ctx *c, int l) {
   DQ_CHECK(compute_expv(c, l));
   const int N = c->N;
-  if (c->precision == 0) {
+  if (c->precision != 2) {
     CK(launch_prop_f64(c->L, 0, c->G64, c->G64, N, N, c->E64m, nullptr, nullptr, nullptr, c->stream));
     CK(launch_prop_f64(c->L, 1, c->G64, c->G64, N, N, c->E64p, nullptr, c->evi64, c->ev64, c->stream));
   } else {
@@ -393,7 +423,7 @@ dqmc_status wrap(dqmc_ctx *c, int l) {
 dqmc_status unwrap(dqmc_ctx *c, int l) {
   DQ_CHECK(compute_expv(c, l));
   const int N = c->N;
-  if (c->precision == 0) {
+  if (c->precision != 2) {
     CK(launch_prop_f64(c->L, 0, c->G64, c->G64, N, N, c->E64p, c->evi64, nullptr, c->ev64, c->stream));
     CK(launch_prop_f64(c->L, 1, c->G64, c->G64, N, N, c->E64m, nullptr, nullptr, nullptr, c->stream));
   } else {
@@ -410,7 +440,12 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
   const int nblk = (N + K - 1) / K;
   T *Gc[2] = {static_cast<T *>(c->Gcol[0]), static_cast<T *>(c->Gcol[1])};
   T *Gr[2] = {static_cast<T *>(c->Grow[0]), static_cast<T *>(c->Grow[1])};
-  CK(launch_gather<T>(N, 0, std::min(K, N), K, G, Gc[0], Gr[0], c->stream));
+  const bool df = (c->precision == 1);
+  if (df)
+    CK(launch_gather_df(N, 0, std::min(K, N), K, (const double *)G, (float2 *)c->Gcol[0],
+                        (double *)c->Grow[0], c->stream));
+  else
+    CK(launch_gather<T>(N, 0, std::min(K, N), K, G, Gc[0], Gr[0], c->stream));
   MetroArgs ma;
   ma.N = N;
   ma.K = K;
@@ -436,15 +471,21 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
     fa.ns0 = (b + 1 < nblk) ? s0 + K : 0;
     fa.nkb = (b + 1 < nblk) ? std::min(K, N - s0 - K) : 0;
     fa.rows_per_cta = 0;
-    CK(launch_flush<T>(K, fa, G, Gc[b & 1], Gr[b & 1], c->Gamma, c->acc, Gc[(b + 1) & 1],
-                       Gr[(b + 1) & 1], c->stream));
+    fa.ldc = K;
+    if (df)
+      CK(launch_flush_df(K, fa, (double *)G, (const float2 *)c->Gcol[b & 1], (const double *)Gr[b & 1],
+                         c->Gamma, c->acc, (float2 *)c->Gcol[(b + 1) & 1], (double *)Gr[(b + 1) & 1],
+                         c->stream));
+    else
+      CK(launch_flush<T>(K, fa, G, Gc[b & 1], Gr[b & 1], c->Gamma, c->acc, Gc[(b + 1) & 1],
+                         Gr[(b + 1) & 1], c->stream));
   }
   c->proposed += N;
   return DQMC_OK;
 }
 
 dqmc_status update_slice(dqmc_ctx *c, int l, int pas) {
-  return c->precision == 0 ? update_slice_t<double>(c, c->G64, l, pas)
+  return c->precision != 2 ? update_slice_t<double>(c, c->G64, l, pas)
                            : update_slice_t<float>(c, c->G32, l, pas);
 }
 
@@ -505,7 +546,7 @@ dqmc_status combine(dqmc_ctx *c, const UDVd &r, const UDVd &lf, double *Gout) {
 dqmc_status refresh(dqmc_ctx *c, int q, bool record_drift) {
   const int N = c->N;
   DQ_CHECK(combine(c, c->right[q], c->left[q], c->Gf));
-  if (c->precision == 0) {
+  if (c->precision != 2) {
     if (record_drift) CK(max_abs_diff_f64(c->Gf, c->G64, N, c->drift, c->stream));
     CK(cudaMemcpyAsync(c->G64, c->Gf, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   } else {
@@ -520,9 +561,22 @@ __global__ void drift_max_kernel(const double *d, double *mx) {
   if (v != v || v > *mx) *mx = v;
 }
 
+// In mixed precision the stabilisation GEMMs of the sweep run as
+// FP64-accurate double-float products on the FP32 units.
+struct GemmModeScope {
+  explicit GemmModeScope(dqmc_ctx *c) {
+    if (c->precision == 1 && c->dfws) {
+      set_df_workspace(c->dfws, c->dfws_elems);
+      set_gemm_df(true);
+    }
+  }
+  ~GemmModeScope() { set_gemm_df(false); }
+};
+
 dqmc_status ensure_ready(dqmc_ctx *c) {
   DQ_CHECK(ensure_alloc(c));
   if (c->ready) return DQMC_OK;
+  GemmModeScope gm(c);
   DQ_CHECK(udv_identity(c, c->left[c->C]));
   for (int q = c->C - 1; q >= 0; --q) {
     std::vector<int> sl;
@@ -556,10 +610,50 @@ dqmc_status measure_now(dqmc_ctx *c) {
   return DQMC_OK;
 }
 
-struct PhaseTimer {
+// Per-phase events (timing >= 1) and, as the thread's kernel sink, per-launch
+// events grouped by kernel family (timing == 2). Also attributes the launches
+// issued while it lives to the context.
+struct PhaseTimer : KTimerSink {
   dqmc_ctx *c;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
-  explicit PhaseTimer(dqmc_ctx *cc) : c(cc) {}
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> kev[KF_COUNT];
+  std::vector<cudaEvent_t> open[KF_COUNT];
+  unsigned long long launches0;
+  double f0[KF_COUNT], b0[KF_COUNT];
+  KTimerSink *prev;
+  explicit PhaseTimer(dqmc_ctx *cc) : c(cc), launches0(launch_count()), prev(ktimer_sink()) {
+    if (c->timing >= 2) ktimer_sink() = this;
+    for (int f = 0; f < KF_COUNT; ++f) {
+      f0[f] = work_flops()[f];
+      b0[f] = work_bytes()[f];
+    }
+  }
+  ~PhaseTimer() override {
+    ktimer_sink() = prev;
+    c->launches += launch_count() - launches0;
+    for (int f = 0; f < KF_COUNT; ++f) {
+      c->flops_kernel[f] += work_flops()[f] - f0[f];
+      c->bytes_kernel[f] += work_bytes()[f] - b0[f];
+    }
+    if (c->timing) {
+      cudaStreamSynchronize(c->stream);
+      collect();
+    }
+  }
+  void begin(int fam, cudaStream_t st) override {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    open[fam].push_back(e);
+  }
+  void end(int fam, cudaStream_t st) override {
+    if (open[fam].empty()) return;
+    cudaEvent_t s = open[fam].back(), e;
+    open[fam].pop_back();
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    kev[fam].push_back({s, e});
+  }
   void start(int ph, cudaEvent_t *e) {
     if (!c->timing) return;
     cudaEventCreate(e);
@@ -585,10 +679,22 @@ struct PhaseTimer {
       }
       ev[ph].clear();
     }
+    for (int f = 0; f < KF_COUNT; ++f) {
+      for (auto &p : kev[f]) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.first, p.second);
+        c->ms_kernel[f] += ms;
+        c->n_kernel[f] += 1;
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+      }
+      kev[f].clear();
+    }
   }
 };
 
 dqmc_status one_sweep(dqmc_ctx *c, bool measure, PhaseTimer &tm) {
+  GemmModeScope gm(c);
   int q = 1;
   cudaEvent_t e0 = nullptr;
   for (int l = 1; l <= c->M; ++l) {
@@ -605,6 +711,7 @@ dqmc_status one_sweep(dqmc_ctx *c, bool measure, PhaseTimer &tm) {
       for (int m = c->tau[q - 1] + 1; m <= c->tau[q]; ++m) sl.push_back(m);
       DQ_CHECK(udv_advance(c, c->right[q - 1], c->right[q], sl, false));
       DQ_CHECK(refresh(c, q, true));
+      DQ_KSCOPE(KF_OTHER, c->stream);
       drift_max_kernel<<<1, 1, 0, c->stream>>>(c->drift, c->drift_max);
       tm.stop(2, e0);
       if (measure) {
@@ -630,6 +737,7 @@ dqmc_status one_sweep(dqmc_ctx *c, bool measure, PhaseTimer &tm) {
       for (int m = c->tau[q + 1]; m > c->tau[q]; --m) sl.push_back(m);
       DQ_CHECK(udv_advance(c, c->left[q + 1], c->left[q], sl, true));
       DQ_CHECK(refresh(c, q, true));
+      DQ_KSCOPE(KF_OTHER, c->stream);
       drift_max_kernel<<<1, 1, 0, c->stream>>>(c->drift, c->drift_max);
       tm.stop(2, e0);
       --q;
@@ -714,13 +822,15 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) {
     if (v < 1 || (double)(int)v != v) return fail(DQMC_EINVAL, "n_stab must be a positive integer");
     c->n_stab = (int)v;
   } else if (k == "precision") {
-    if (v != 0.0 && v != 1.0) return fail(DQMC_EINVAL, "precision must be 0 (fp64) or 1 (mixed)");
+    if (v != 0.0 && v != 1.0 && v != 2.0)
+      return fail(DQMC_EINVAL, "precision must be 0 (fp64), 1 (mixed) or 2 (fp32)");
     c->precision = (int)v;
   } else if (k == "chain") {
     if (v < 0 || v > 0xffffff || (double)(int)v != v) return fail(DQMC_EINVAL, "chain must be in [0, 2^24)");
     c->chain = (int)v;
   } else if (k == "timing") {
-    c->timing = v != 0.0;
+    if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "timing must be 0, 1 or 2");
+    c->timing = (int)v;
   } else if (k == "site_offsets") {
     c->site_offsets = v != 0.0;
   } else if (k == "bin") {
@@ -783,6 +893,7 @@ dqmc_status dqmc_green(dqmc_ctx *c, int slice, double *G_out) {
   DQ_CHECK(check_ctx(c));
   if (!G_out) return fail(DQMC_EINVAL, "G_out is NULL");
   if (slice < 0 || slice > c->M) return fail(DQMC_EINVAL, "slice out of range");
+  PhaseTimer tm(c);
   DQ_CHECK(ensure_ready(c));
   // right chain B(slice, 0) in tmpA, left chain B(beta, slice)^T in tmpB, QR every n_stab slices
   DQ_CHECK(udv_identity(c, c->tmpA));
@@ -806,9 +917,10 @@ dqmc_status dqmc_green(dqmc_ctx *c, int slice, double *G_out) {
 dqmc_status dqmc_get_running_green(dqmc_ctx *c, double *G_out, int *slice) {
   DQ_CHECK(check_ctx(c));
   if (!G_out) return fail(DQMC_EINVAL, "G_out is NULL");
+  PhaseTimer tm(c);
   DQ_CHECK(ensure_ready(c));
   const size_t NN = (size_t)c->N * c->N;
-  if (c->precision == 0) {
+  if (c->precision != 2) {
     CK(cudaMemcpyAsync(G_out, c->G64, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   } else {
     CK(convert_f32_to_f64(c->G32, c->X, (long)NN, c->stream));
@@ -908,6 +1020,13 @@ dqmc_status dqmc_get_stats(dqmc_ctx *c, dqmc_stats *o) {
   o->ms_update = c->ms_update;
   o->ms_stab = c->ms_stab;
   o->ms_measure = c->ms_measure;
+  for (int f = 0; f < KF_COUNT; ++f) {
+    o->ms_kernel[f] = c->ms_kernel[f];
+    o->n_kernel[f] = c->n_kernel[f];
+    o->flops_kernel[f] = c->flops_kernel[f];
+    o->bytes_kernel[f] = c->bytes_kernel[f];
+  }
+  o->launches = c->launches;
   return DQMC_OK;
 }
 
@@ -926,6 +1045,7 @@ dqmc_status dqmc_set_field(dqmc_ctx *c, const int8_t *s) {
   const size_t n = (size_t)c->M * c->N;
   for (size_t q = 0; q < n; ++q)
     if (s[q] != 1 && s[q] != -1) return fail(DQMC_EINVAL, "field values must be +1 or -1");
+  PhaseTimer tm(c);
   DQ_CHECK(ensure_alloc(c));
   CK(cudaMemcpyAsync(c->field, s, n, cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));

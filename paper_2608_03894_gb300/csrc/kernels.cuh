@@ -36,11 +36,19 @@ struct FlushArgs {
   int N, s0, kb;   // current block
   int ns0, nkb;    // next block (nkb = 0: none)
   int rows_per_cta;
+  int ldc;         // row stride of Gcol (>= kb); the next-block Gcol uses stride K
 };
 template <typename T>
 cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
                          const double *Gamma, const int *acc, T *Gcol_next, T *Grow_next,
                          cudaStream_t st);
+// FP64-accurate flush on the FP32 units: G and Grow FP64, Gcol as (hi, lo)
+// FP32 pairs (stride K, zero beyond kb), next-block Gcol written split.
+cudaError_t launch_flush_df(int K, const FlushArgs &a, double *G, const float2 *Gcol,
+                            const double *Grow, const double *Gamma, const int *acc,
+                            float2 *Gcol_next, double *Grow_next, cudaStream_t st);
+cudaError_t launch_gather_df(int N, int s0, int kb, int K, const double *G, float2 *Gcol,
+                             double *Grow, cudaStream_t st);
 
 // ---- measurement (measure.cu)
 struct MeasTables {

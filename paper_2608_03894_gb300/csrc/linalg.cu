@@ -121,11 +121,20 @@ static int grid_for(long work, int per = 256) {
   return (int)g;
 }
 
+cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
+  scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
+  return cudaGetLastError();
+}
+
 cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
                   const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
                   const double *cs, cudaStream_t st, int splitk) {
   if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K > 0 && gemm_df())
+    return dfgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, st, splitk, 304);
   if (K <= 0) {
+    DQ_KSCOPE(KF_OTHER, st);
     scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
     return cudaGetLastError();
   }
@@ -145,9 +154,13 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
   splitk = (K + klen - 1) / klen;
   const int atomic = splitk > 1;
   if (atomic) {
+    DQ_KSCOPE(KF_OTHER, st);
     scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
   }
   dim3 grid((N + 63) / 64, (M + 63) / 64, splitk);
+  DQ_KSCOPE(KF_GEMM, st);
+  add_work(KF_GEMM, 2.0 * M * (double)N * K,
+           8.0 * ((double)M * K + (double)K * N + (beta != 0.0 ? 2.0 : 1.0) * (double)M * N));
   if (!ta && !tb)
     dgemm_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
   else if (ta && !tb)
@@ -362,6 +375,9 @@ static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, c
   cudaError_t e = cudaFuncSetAttribute(qr_panel_kernel<NB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  DQ_KSCOPE(KF_QRPANEL, st);
+  // Householder panel: ~4 m nc^2 flops; the m x nc panel read and written once
+  add_work(KF_QRPANEL, 4.0 * (n - p) * (double)nc * nc, 16.0 * (n - p) * (double)nc);
   qr_panel_kernel<NB><<<kClusterCTAs, 256, smem, st>>>(A, n, p, nc, w.V, w.Y, w.Y2, w.tau);
   return cudaGetLastError();
 }
@@ -451,6 +467,7 @@ cudaError_t qr_solve_r(const double *A, int n, double *B, double *Z, int ncols, 
                        cudaStream_t st) {
   const int nb = w.nb;
   const int nblk = (n + nb - 1) / nb;
+  DQ_KSCOPE(KF_OTHER, st);
   tri_inv_upper_blocks_kernel<<<nblk, 64, (size_t)nb * nb * sizeof(double), st>>>(A, n, nb, w.Rinv);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -482,6 +499,7 @@ __global__ void set_identity_kernel(double *A, int n, int ld) {
   }
 }
 cudaError_t set_identity(double *A, int n, int ld, cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
   set_identity_kernel<<<grid_for((long)n * n), 256, 0, st>>>(A, n, ld);
   return cudaGetLastError();
 }
@@ -491,6 +509,7 @@ __global__ void set_value_kernel(double *x, long n, double v) {
     x[e] = v;
 }
 cudaError_t set_value(double *x, long n, double v, cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
   set_value_kernel<<<grid_for(n), 256, 0, st>>>(x, n, v);
   return cudaGetLastError();
 }
@@ -513,6 +532,7 @@ __global__ void transpose_scale_kernel(const double *in, int ld, double *out, in
 cudaError_t transpose_scale(const double *in, int ld, double *out, int n, const double *rs,
                             cudaStream_t st) {
   dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  DQ_KSCOPE(KF_OTHER, st);
   transpose_scale_kernel<<<grid, block, 0, st>>>(in, ld, out, n, rs);
   return cudaGetLastError();
 }
@@ -530,6 +550,7 @@ __global__ void scale_rows_cols_kernel(double *X, int n, int ld, const double *r
 }
 cudaError_t scale_rows_cols(double *X, int n, int ld, const double *rs, const double *cs,
                             cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
   scale_rows_cols_kernel<<<grid_for((long)n * n), 256, 0, st>>>(X, n, ld, rs, cs);
   return cudaGetLastError();
 }
@@ -546,6 +567,7 @@ __global__ void column_norms_kernel(const double *X, int n, const double *D, dou
 }
 cudaError_t column_norms_scaled(const double *X, int n, const double *D, double *norms,
                                 cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
   column_norms_kernel<<<(n + 127) / 128, 128, 0, st>>>(X, n, D, norms);
   return cudaGetLastError();
 }
@@ -594,6 +616,7 @@ cudaError_t argsort_desc(const double *key, int n, int *perm, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(argsort_desc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  DQ_KSCOPE(KF_OTHER, st);
   argsort_desc_kernel<<<1, 1024, smem, st>>>(key, n, np, perm);
   return cudaGetLastError();
 }
@@ -611,6 +634,7 @@ __global__ void permute_udv_kernel(const double *X, const double *D, const doubl
 }
 cudaError_t permute_udv(const double *X, const double *D, const double *T, const int *perm, int n,
                         double *Xp, double *Dp, double *Tp, cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
   permute_udv_kernel<<<grid_for((long)n * n), 256, 0, st>>>(X, D, T, perm, n, Xp, Dp, Tp);
   return cudaGetLastError();
 }
@@ -628,7 +652,11 @@ __global__ void udv_scale_kernel(double *R, int n, const double *Dp, const doubl
   }
 }
 cudaError_t udv_diag_and_scale(double *R, int n, const double *Dp, double *Dnew, cudaStream_t st) {
-  udv_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(R, n, Dp, Dnew);
+  {
+    DQ_KSCOPE(KF_OTHER, st);
+    udv_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(R, n, Dp, Dnew);
+  }
+  DQ_KSCOPE(KF_OTHER, st);
   udv_scale_kernel<<<grid_for((long)n * n), 256, 0, st>>>(R, n, Dp, Dnew);
   return cudaGetLastError();
 }
@@ -655,12 +683,14 @@ __global__ void max_abs_diff_kernel(const double *A, const TB *B, long total, do
 cudaError_t max_abs_diff_f64(const double *A, const double *B, int n, double *out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
+  DQ_KSCOPE(KF_OTHER, st);
   max_abs_diff_kernel<double><<<grid_for((long)n * n, 1024), 256, 0, st>>>(A, B, (long)n * n, out);
   return cudaGetLastError();
 }
 cudaError_t max_abs_diff_f32(const double *A, const float *B, int n, double *out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
+  DQ_KSCOPE(KF_OTHER, st);
   max_abs_diff_kernel<float><<<grid_for((long)n * n, 1024), 256, 0, st>>>(A, B, (long)n * n, out);
   return cudaGetLastError();
 }
@@ -674,10 +704,12 @@ __global__ void f32_to_f64_kernel(const float *A, double *B, long n) {
     B[e] = (double)A[e];
 }
 cudaError_t convert_f64_to_f32(const double *A, float *B, long n, cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
   f64_to_f32_kernel<<<grid_for(n), 256, 0, st>>>(A, B, n);
   return cudaGetLastError();
 }
 cudaError_t convert_f32_to_f64(const float *A, double *B, long n, cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
   f32_to_f64_kernel<<<grid_for(n), 256, 0, st>>>(A, B, n);
   return cudaGetLastError();
 }
@@ -691,6 +723,7 @@ __global__ void split_scales_kernel(const double *D, int n, double *dmax_inv, do
   }
 }
 cudaError_t split_scales(const double *D, int n, double *dmax_inv, double *dmin, cudaStream_t st) {
+  DQ_KSCOPE(KF_OTHER, st);
   split_scales_kernel<<<(n + 255) / 256, 256, 0, st>>>(D, n, dmax_inv, dmin);
   return cudaGetLastError();
 }

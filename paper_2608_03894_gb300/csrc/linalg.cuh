@@ -9,9 +9,19 @@ namespace dq {
 // A is M x K (lda) or, transposed, K x M; B is K x N (ldb) or N x K.
 // splitk > 1 splits K over CTAs and accumulates with atomics (C is first
 // scaled by beta in a separate pass).
+// While set_gemm_df(true) is in effect for the calling thread (and a
+// workspace is bound), dgemm runs as dfgemm: FP64 in and out, FP64-accurate
+// products computed on the FP32 units from (hi, lo) FP32 pairs.
 cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
                   const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
                   const double *cs, cudaStream_t st, int splitk = 0);
+cudaError_t dfgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
+                   const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
+                   const double *cs, cudaStream_t st, int splitk, int tiles_target);
+void set_df_workspace(float2 *ws, size_t elems);  // >= max over calls of M*K + K*N pairs
+void set_gemm_df(bool on);
+bool gemm_df();
+cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st);
 
 // Householder QR workspace for an n x n matrix: V (unit lower trapezoidal,
 // explicit), Y = V T^T and Y2 = V T per panel (panel p in columns p..p+nb),

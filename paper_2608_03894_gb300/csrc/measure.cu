@@ -97,8 +97,12 @@ cudaError_t launch_measure(const double *G, int N, const MeasTables &t, double *
   cudaError_t e = cudaMemsetAsync(raw, 0, kMeasRaw * sizeof(double), st);
   if (e != cudaSuccess) return e;
   dim3 grid((N + 31) / 32, (N + 31) / 32), block(32, 8);
+  DQ_KSCOPE(KF_MEASURE, st);
+  add_work(KF_MEASURE, 12.0 * N * (double)N, 8.0 * N * (double)N);
   measure_tile_kernel<<<grid, block, 0, st>>>(G, N, t, raw);
+  DQ_KSCOPE(KF_MEASURE, st);
   measure_diag_kernel<<<(N + 255) / 256, 256, 0, st>>>(G, N, t, raw);
+  DQ_KSCOPE(KF_MEASURE, st);
   measure_finalize_kernel<<<1, 1, 0, st>>>(raw, N, thop, t.wkc != nullptr, obs);
   return cudaGetLastError();
 }

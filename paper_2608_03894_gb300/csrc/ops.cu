@@ -120,8 +120,7 @@ static dqmc_status op_flush(int N, int site0, int kb, T *G, const T *Gcol, const
   if (!G || !Gcol || !Grow || !Gamma) return fail(DQMC_EINVAL, "null pointer");
   int K = 4;
   while (K < kb) K <<= 1;
-  if (K != kb) return fail(DQMC_EINVAL, "operator flush takes kb in {4, 8, 16, 32, 64}");
-  FlushArgs a{N, site0, kb, 0, 0, 0};
+  FlushArgs a{N, site0, kb, 0, 0, 0, kb};
   DQ_CUDA(launch_flush<T>(K, a, G, Gcol, Grow, Gamma, nullptr, nullptr, nullptr,
                           static_cast<cudaStream_t>(stream)));
   return DQMC_OK;

@@ -211,6 +211,14 @@ cudaError_t launch_prop_L(int side, const T *X, T *Y, int nvec, int ld, const cp
   using C = PropCfg<T, L>;
   const int grid = (nvec + C::VT - 1) / C::VT;
   if (grid == 0) return cudaSuccess;
+  DQ_KSCOPE(KF_PROP, st);
+  // one read and one write of the N x nvec operand; flops per vector
+  // 15 L^2 log2(L^2) + 36 L^2 (real-input FFTs both ways plus the 3x3 blocks)
+  {
+    const double L2 = (double)L * L;
+    const double lg = L > 1 ? std::log2(L2) : 0.0;
+    add_work(KF_PROP, (15.0 * L2 * lg + 36.0 * L2) * nvec, 2.0 * C::N * (double)nvec * sizeof(T));
+  }
   if (side == 0) {
     cudaError_t e = ensure_smem_attr((const void *)prop_kernel<T, L, 0>, C::kSmem);
     if (e != cudaSuccess) return e;

@@ -10,6 +10,8 @@
 // The block's serial loop runs in one CTA in FP64 (ratios and bookkeeping);
 // the flush is one rank-k product over the whole N x N G in the working
 // precision, and its epilogue gathers G[:,S'] and G[S',:] of the next block.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace dq {
@@ -41,6 +43,7 @@ cudaError_t launch_gather(int N, int s0, int kb, int K, const T *G, T *Gcol, T *
   int grid = (int)((work + 255) / 256);
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
+  DQ_KSCOPE(KF_OTHER, st);
   gather_block_kernel<T><<<grid, 256, 0, st>>>(N, s0, kb, K, G, Gcol, Grow);
   return cudaGetLastError();
 }
@@ -166,6 +169,7 @@ cudaError_t launch_metropolis(const MetroArgs &a, const TG *g, int8_t *s, const 
   cudaError_t e = ensure_smem_attr((const void *)metropolis_block_kernel<TG>,
                                    (int)(5 * 64 * 65 * sizeof(double)));
   if (e != cudaSuccess) return e;
+  DQ_KSCOPE(KF_METRO, st);
   metropolis_block_kernel<TG><<<1, threads, smem, st>>>(a, g, s, forced, Gamma, accept_count,
                                                          status, total);
   return cudaGetLastError();
@@ -178,64 +182,118 @@ template cudaError_t launch_metropolis<float>(const MetroArgs &, const float *, 
                                               unsigned long long *, cudaStream_t);
 
 // ----------------------------------------------------------------- rank-k flush
-// G[:, J] -= Gcol * W_J,  W_J = Gamma (E_S - Grow)[:, J], one CTA per
-// (32-column stripe J, row chunk). Lane = column of J; warp w owns rows
-// i = r0 + w, r0 + w + 8, ... Each thread keeps its column of W_J (K values)
-// in registers and streams G[i, j] once: read, subtract, write. The epilogue
-// also gathers the next block (rows / columns S' = [ns0, ns0 + nkb)).
+// G[:, J] -= Gcol W_J, W_J = Gamma (E_S - Grow)[:, J], one CTA per stripe J
+// of SW consecutive columns covering all N rows, so W_J (K x SW) is formed
+// once. Thread (rsub, col) owns column j0 + col and rows rsub, rsub + 256/SW,
+// ...; it keeps its column of W in registers and streams G once (read,
+// subtract, write). The epilogue gathers the next block's rows / columns.
+//   T  = storage type of G (double or float)
+//   DF = FP64-accurate product on the FP32 units: Gcol holds (hi, lo) FP32
+//        pairs, W is split in registers, each MAC is an exact FP32 product
+//        plus cross terms accumulated with TwoSum (T must be double).
+__device__ __forceinline__ void df_mac2(float ah, float al, float bh, float bl, float &sh, float &sl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = sh + p;
+  const float z = t - sh;
+  const float err = (sh - (t - z)) + (p - z);
+  sh = t;
+  sl += err + e;
+}
 
-template <typename T, int K>
+template <typename T, int K, int SW, bool DF>
 __global__ void __launch_bounds__(256)
-    flush_kernel(FlushArgs a, T *__restrict__ G, const T *__restrict__ Gcol,
+    flush_kernel(FlushArgs a, T *__restrict__ G, const void *__restrict__ Gcol_,
                  const T *__restrict__ Grow, const double *__restrict__ Gamma,
-                 const int *__restrict__ accept_count, T *__restrict__ Gcol_next,
+                 const int *__restrict__ accept_count, void *__restrict__ Gcol_next_,
                  T *__restrict__ Grow_next) {
-  __shared__ double Wsh[K][33];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int RSTEP = 256 / SW;
+  __shared__ double Wsh[K][SW];
+  const int tid = threadIdx.x, col = tid % SW, rsub = tid / SW;
   const int N = a.N;
-  const int j = blockIdx.x * 32 + lane;
+  const int j0 = blockIdx.x * SW, j = j0 + col;
   const bool jok = j < N;
   const int m_acc = accept_count ? *accept_count : 1;
 
-  // W_J[p][lane] = Gamma[p][j - s0] (if j in S) - sum_q Gamma[p][q] Grow[q][j]
   if (m_acc > 0) {
-    for (int p = warp; p < K; p += 8) {
+    for (int e = tid; e < K * SW; e += 256) {
+      const int p = e / SW, c = e % SW, jj = j0 + c;
       double w = 0.0;
-      if (jok && p < a.kb) {
-        const int js = j - a.s0;
+      if (jj < N && p < a.kb) {
+        const int js = jj - a.s0;
         if (js >= 0 && js < a.kb) w = Gamma[p * K + js];
-        for (int q = 0; q < a.kb; ++q) w -= Gamma[p * K + q] * (double)Grow[(size_t)q * N + j];
+        for (int q = 0; q < a.kb; ++q) w -= Gamma[p * K + q] * (double)Grow[(size_t)q * N + jj];
       }
-      Wsh[p][lane] = w;
+      Wsh[p][c] = w;
     }
   }
   __syncthreads();
-  T wreg[K];
-#pragma unroll
-  for (int p = 0; p < K; ++p) wreg[p] = (m_acc > 0) ? (T)Wsh[p][lane] : T(0);
 
-  const int r0 = blockIdx.y * a.rows_per_cta;
-  const int r1 = min(N, r0 + a.rows_per_cta);
-  for (int i = r0 + warp; i < r1; i += 8) {
-    if (!jok) continue;
-    const T *gc = Gcol + (size_t)i * K;
+  using WT = typename std::conditional<DF, float, T>::type;
+  WT wh[K], wl[DF ? K : 1];
+#pragma unroll
+  for (int p = 0; p < K; ++p) {
+    const double w = (m_acc > 0) ? Wsh[p][col] : 0.0;
+    if constexpr (DF) {
+      wh[p] = (float)w;
+      wl[p] = (float)(w - (double)wh[p]);
+    } else {
+      wh[p] = (T)w;
+    }
+  }
+  if (!jok) return;
+
+  for (int i = rsub; i < N; i += RSTEP) {
     T acc = T(0);
     if (m_acc > 0) {
+      if constexpr (DF) {
+        const float2 *gc = static_cast<const float2 *>(Gcol_) + (size_t)i * a.ldc;
+        float sh = 0.f, sl = 0.f;
+        if ((a.ldc & 1) == 0) {
 #pragma unroll
-      for (int p = 0; p < K; p += 4) {
-        if constexpr (sizeof(T) == 4) {
-          const float4 g4 = *reinterpret_cast<const float4 *>(gc + p);
-          acc = fmaf(g4.x, wreg[p], acc);
-          acc = fmaf(g4.y, wreg[p + 1], acc);
-          acc = fmaf(g4.z, wreg[p + 2], acc);
-          acc = fmaf(g4.w, wreg[p + 3], acc);
+          for (int p = 0; p < K; p += 2) {
+            if (p < a.kb) {
+              const float4 g = *reinterpret_cast<const float4 *>(gc + p);
+              df_mac2(g.x, g.y, wh[p], wl[p], sh, sl);
+              df_mac2(g.z, g.w, wh[p + 1], wl[p + 1], sh, sl);
+            }
+          }
         } else {
-          const double2 g0 = *reinterpret_cast<const double2 *>(gc + p);
-          const double2 g1 = *reinterpret_cast<const double2 *>(gc + p + 2);
-          acc = fma(g0.x, wreg[p], acc);
-          acc = fma(g0.y, wreg[p + 1], acc);
-          acc = fma(g1.x, wreg[p + 2], acc);
-          acc = fma(g1.y, wreg[p + 3], acc);
+#pragma unroll
+          for (int p = 0; p < K; ++p)
+            if (p < a.kb) df_mac2(gc[p].x, gc[p].y, wh[p], wl[p], sh, sl);
+        }
+        acc = (double)sh + (double)sl;
+      } else {
+        const T *gc = static_cast<const T *>(Gcol_) + (size_t)i * a.ldc;
+        if ((a.ldc & 3) == 0) {
+          // 16-byte vector loads; a group straddling kb stays inside the row
+          // (ldc >= kb rounded up to 4) and meets zero rows of W
+#pragma unroll
+          for (int p = 0; p < K; p += 4) {
+            if (p < a.kb) {
+              if constexpr (sizeof(T) == 4) {
+                const float4 g4 = *reinterpret_cast<const float4 *>(gc + p);
+                acc = fmaf(g4.x, wh[p], acc);
+                acc = fmaf(g4.y, wh[p + 1], acc);
+                acc = fmaf(g4.z, wh[p + 2], acc);
+                acc = fmaf(g4.w, wh[p + 3], acc);
+              } else {
+                const double2 g0 = *reinterpret_cast<const double2 *>(gc + p);
+                const double2 g1 = *reinterpret_cast<const double2 *>(gc + p + 2);
+                acc = fma(g0.x, wh[p], acc);
+                acc = fma(g0.y, wh[p + 1], acc);
+                acc = fma(g1.x, wh[p + 2], acc);
+                acc = fma(g1.y, wh[p + 3], acc);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int p = 0; p < K; ++p)
+            if (p < a.kb) acc = fma(gc[p], wh[p], acc);
         }
       }
     }
@@ -245,42 +303,57 @@ __global__ void __launch_bounds__(256)
     if (a.nkb > 0) {
       const int it = i - a.ns0, jt = j - a.ns0;
       if (it >= 0 && it < a.nkb) Grow_next[(size_t)it * N + j] = val;
-      if (jt >= 0 && jt < K) Gcol_next[(size_t)i * K + jt] = (jt < a.nkb) ? val : T(0);
+      if (jt >= 0 && jt < K) {
+        if constexpr (DF) {
+          float2 *gn = static_cast<float2 *>(Gcol_next_) + (size_t)i * K + jt;
+          if (jt < a.nkb) {
+            const float h = (float)val;
+            *gn = make_float2(h, (float)(val - (double)h));
+          } else {
+            *gn = make_float2(0.f, 0.f);
+          }
+        } else {
+          static_cast<T *>(Gcol_next_)[(size_t)i * K + jt] = (jt < a.nkb) ? val : T(0);
+        }
+      }
     }
   }
 }
 
-template <typename T, int K>
-static cudaError_t launch_flush_K(const FlushArgs &a0, T *G, const T *Gcol, const T *Grow,
-                                  const double *Gamma, const int *acc, T *Gcol_next, T *Grow_next,
-                                  cudaStream_t st) {
-  FlushArgs a = a0;
-  const int stripes = (a.N + 31) / 32;
-  // enough CTAs to cover ~2 waves of 152 SMs
-  int chunks = (304 + stripes - 1) / stripes;
-  if (chunks < 1) chunks = 1;
-  a.rows_per_cta = (a.N + chunks - 1) / chunks;
-  a.rows_per_cta = ((a.rows_per_cta + 7) / 8) * 8;
-  chunks = (a.N + a.rows_per_cta - 1) / a.rows_per_cta;
-  dim3 grid(stripes, chunks);
-  flush_kernel<T, K><<<grid, 256, 0, st>>>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next);
-  // Gcol_next columns jt in [nkb, K) of rows not visited stay as they were:
-  // the gather zero-fills them on allocation and after a ragged block.
+template <typename T, int K, bool DF>
+static cudaError_t launch_flush_K(const FlushArgs &a, T *G, const void *Gcol, const T *Grow,
+                                  const double *Gamma, const int *acc, void *Gcol_next,
+                                  T *Grow_next, cudaStream_t st) {
+  constexpr int SW = 4;
+  const int grid = (a.N + SW - 1) / SW;
+  DQ_KSCOPE(KF_FLUSH, st);
+  // rank-kb update of the N x N G: 2 N^2 kb flops (+ 2 kb^2 N for W); G read
+  // and written once, Gcol and Grow read once
+  add_work(KF_FLUSH, 2.0 * a.N * (double)a.N * a.kb + 2.0 * a.kb * (double)a.kb * a.N,
+           (2.0 * a.N * (double)a.N + 2.0 * a.N * (double)a.kb) * sizeof(T));
+  flush_kernel<T, K, SW, DF><<<grid, 256, 0, st>>>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next);
   return cudaGetLastError();
+}
+
+template <typename T, bool DF>
+static cudaError_t launch_flush_any(int K, const FlushArgs &a, T *G, const void *Gcol, const T *Grow,
+                                    const double *Gamma, const int *acc, void *Gcol_next, T *Grow_next,
+                                    cudaStream_t st) {
+  switch (K) {
+    case 4: return launch_flush_K<T, 4, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
+    case 8: return launch_flush_K<T, 8, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
+    case 16: return launch_flush_K<T, 16, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
+    case 32: return launch_flush_K<T, 32, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
+    case 64: return launch_flush_K<T, 64, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>
 cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
                          const double *Gamma, const int *acc, T *Gcol_next, T *Grow_next,
                          cudaStream_t st) {
-  switch (K) {
-    case 4: return launch_flush_K<T, 4>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    case 8: return launch_flush_K<T, 8>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    case 16: return launch_flush_K<T, 16>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    case 32: return launch_flush_K<T, 32>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    case 64: return launch_flush_K<T, 64>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_flush_any<T, false>(K, a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
 }
 template cudaError_t launch_flush<double>(int, const FlushArgs &, double *, const double *,
                                           const double *, const double *, const int *, double *,
@@ -288,5 +361,45 @@ template cudaError_t launch_flush<double>(int, const FlushArgs &, double *, cons
 template cudaError_t launch_flush<float>(int, const FlushArgs &, float *, const float *,
                                          const float *, const double *, const int *, float *,
                                          float *, cudaStream_t);
+
+cudaError_t launch_flush_df(int K, const FlushArgs &a, double *G, const float2 *Gcol,
+                            const double *Grow, const double *Gamma, const int *acc,
+                            float2 *Gcol_next, double *Grow_next, cudaStream_t st) {
+  return launch_flush_any<double, true>(K, a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
+}
+
+// Gather for the double-float flush: Gcol as (hi, lo) FP32 pairs, Grow in FP64.
+__global__ void gather_block_df_kernel(int N, int s0, int kb, int K, const double *__restrict__ G,
+                                       float2 *__restrict__ Gcol, double *__restrict__ Grow) {
+  const long total = (long)N * K;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / K), t = (int)(e % K);
+    float2 v = make_float2(0.f, 0.f);
+    if (t < kb) {
+      const double x = G[(size_t)i * N + s0 + t];
+      const float h = (float)x;
+      v = make_float2(h, (float)(x - (double)h));
+    }
+    Gcol[e] = v;
+  }
+  const long total2 = (long)kb * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total2;
+       e += (long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / N), j = (int)(e % N);
+    Grow[e] = G[(size_t)(s0 + t) * N + j];
+  }
+}
+
+cudaError_t launch_gather_df(int N, int s0, int kb, int K, const double *G, float2 *Gcol,
+                             double *Grow, cudaStream_t st) {
+  const long work = (long)N * K;
+  int grid = (int)((work + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  DQ_KSCOPE(KF_OTHER, st);
+  gather_block_df_kernel<<<grid, 256, 0, st>>>(N, s0, kb, K, G, Gcol, Grow);
+  return cudaGetLastError();
+}
 
 }  // namespace dq

@@ -60,8 +60,8 @@ class DQMC:
         self.N = 3 * self.L * self.L
         self.M = int(round(beta / dtau))
         self._alloc = None
-        prec = {"fp64": 0, "mixed": 1, 0: 0, 1: 1}[precision]
-        opts = dict(k=k, n_stab=n_stab, precision=prec, chain=chain, timing=int(bool(timing)),
+        prec = {"fp64": 0, "mixed": 1, "fp32": 2, 0: 0, 1: 1, 2: 2}[precision]
+        opts = dict(k=k, n_stab=n_stab, precision=prec, chain=chain, timing=int(timing),
                     site_offsets=int(bool(site_offsets)), bin=bin, drift_limit=drift_limit)
         for key, v in opts.items():
             self.set_option(key, v)
@@ -106,7 +106,11 @@ class DQMC:
     def stats(self):
         s = _lib.Stats()
         check(self.lib.dqmc_get_stats(self.h, C.byref(s)))
-        return {n: getattr(s, n) for n, _ in _lib.Stats._fields_}
+        arrays = ("ms_kernel", "n_kernel", "flops_kernel", "bytes_kernel")
+        out = {n: getattr(s, n) for n, _ in _lib.Stats._fields_ if n not in arrays}
+        for n in arrays:
+            out[n] = dict(zip(_lib.KERNEL_FAMILIES, list(getattr(s, n))))
+        return out
 
     @property
     def field(self):

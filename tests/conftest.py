@@ -16,3 +16,14 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+def build_library():
+    """Compile the CUDA library if needed (loaded by path: importing the
+    package would try to load the library first)."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2608_03894_gb300", "_build.py")
+    spec = importlib.util.spec_from_file_location("_dqmc_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()

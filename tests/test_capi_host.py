@@ -8,13 +8,12 @@ import re
 
 import pytest
 
-from conftest import ROOT
+from conftest import ROOT, build_library
 
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2608_03894_gb300 import _build
-    _build.build()
+    build_library()
     from paper_2608_03894_gb300 import _lib
     return _lib.load()
 
@@ -37,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
-def test_binding_covers_every_symbol():
+def test_binding_covers_every_symbol(lib):
     from paper_2608_03894_gb300 import _lib
     assert set(header_functions()) == set(_lib.SIGNATURES)
 
@@ -68,7 +67,9 @@ def test_create_and_destroy_without_gpu_work(lib):
     assert st == 0 and h.value
     assert lib.dqmc_set_option(h, b"k", 16.0) == 0
     assert lib.dqmc_set_option(h, b"k", 7.0) == 1
-    assert lib.dqmc_set_option(h, b"precision", 2.0) == 1
+    assert lib.dqmc_set_option(h, b"precision", 2.0) == 0
+    assert lib.dqmc_set_option(h, b"precision", 3.0) == 1
+    assert lib.dqmc_set_option(h, b"timing", 5.0) == 1
     assert lib.dqmc_set_option(h, b"nonsense", 1.0) == 1
     assert lib.dqmc_set_option(h, b"n_stab", 0.0) == 1
     assert lib.dqmc_set_option(h, b"drift_limit", -1.0) == 1

@@ -26,6 +26,8 @@ torch = pytest.importorskip("torch")
 def pkg():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from conftest import build_library
+    build_library()
     import paper_2608_03894_gb300 as p
     return p
 
@@ -192,14 +194,16 @@ def test_u0_closed_form_on_gpu(pkg):
         assert np.max(np.abs(G - m.green_free())) < 1e-10
 
 
-@pytest.mark.parametrize("L,k,n_stab,beta", [(4, 8, 10, 2.0), (6, 16, 5, 1.0), (2, 4, 3, 0.7)])
-def test_identical_field_history_20_sweeps(pkg, L, k, n_stab, beta):
+@pytest.mark.parametrize("L,k,n_stab,beta,prec", [(4, 8, 10, 2.0, "fp64"), (6, 16, 5, 1.0, "fp64"),
+                                                 (2, 4, 3, 0.7, "fp64"), (4, 8, 10, 2.0, "mixed"),
+                                                 (6, 32, 5, 1.0, "mixed")])
+def test_identical_field_history_20_sweeps(pkg, L, k, n_stab, beta, prec):
     """Fed the same Philox stream, the GPU chain makes exactly the oracle's
     decisions for 20 sweeps (fields bit-identical after every sweep) and its G
-    stays within 1e-10."""
+    stays within 1e-10 -- in FP64 and in the FP64-accurate mixed mode."""
     par = dict(L=L, beta=beta, dtau=0.1, U=-4.0, mu=-1.0)
     ref = odqmc.Chain(**par, seed=1, n_stab=n_stab)
-    with pkg.DQMC(**par, seed=1, k=k, n_stab=n_stab) as d:
+    with pkg.DQMC(**par, seed=1, k=k, n_stab=n_stab, precision=prec) as d:
         assert np.array_equal(d.field, ref.field)
         for s in range(20):
             d.sweep(1)
@@ -234,6 +238,17 @@ def test_mixed_precision_drift_L12(pkg):
         G, sl = d.running_green()
         Gf = ogreen.green_udv(m, d.field, sl)
         assert np.max(np.abs(G - Gf)) <= 1e-6
+
+
+def test_plain_fp32_mode_runs_and_reports_its_drift(pkg):
+    """Plain FP32 wraps and flushes are available as precision "fp32"; their
+    rounding is amplified by cond(B_l) between refreshes, so the drift is far
+    above FP64's. The test checks the mode runs and reports a finite drift."""
+    par = dict(L=4, beta=2.0, dtau=0.1, U=-4.0, mu=-1.0)
+    with pkg.DQMC(**par, seed=1, k=8, n_stab=10, precision="fp32", drift_limit=10.0) as d:
+        d.sweep(1)
+        drift = d.stats()["max_drift"]
+        assert np.isfinite(drift) and drift > 1e-8
 
 
 def test_checkpoint_resume_is_exact(pkg, tmp_path):
