@@ -109,9 +109,12 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  * "timing" (1 = per-phase CUDA-event timers, 2 = also per kernel family; the
  * events themselves cost time, so time throughput with 0), "site_offsets" (1 = S_Pair phases
  * use site positions R + tau_a, 0 = cell positions), "bin" (measurements per
- * bin, default 10), "drift_limit" (hard limit, default 1e-3 -> DQMC_ENUMERIC).
- * "k", "n_stab", "precision" and "chain" are accepted only before the first
- * sweep; later they return DQMC_ESTATE. */
+ * bin, default 10), "drift_limit" (hard limit, default 1e-3 -> DQMC_ENUMERIC),
+ * "df_flush" / "df_stab" (mixed precision only, default 1: run the rank-m
+ * flush / the stabilisation GEMMs as double-float products; 0 = native FP64).
+ * "k", "n_stab", "precision", "chain", "df_flush" and "df_stab" are accepted
+ * only before the first sweep; later they return DQMC_ESTATE. Precision 2
+ * ("fp32") runs plain FP32 propagation and flush. */
 dqmc_status dqmc_set_option(dqmc_ctx *ctx, const char *key, double value);
 
 /* Launch every kernel of this context on the given cudaStream_t (e.g. the
@@ -187,28 +190,49 @@ dqmc_status dqmc_op_propagate_f32(int L, double scale, int side, const float *X,
                                   int nvec, int ld, const float *pre, const float *post,
                                   const float *vscale, void *stream);
 
-/* Delayed-update block (one CTA, FP64 bookkeeping): propose the kb <= 64 sites
+/* Delayed-update block (one CTA, FP64 bookkeeping; the delayed update the
+ * paper combines with its FFT propagation): propose the kb <= 64 sites
  * S = [site0, site0+kb) of slice `slice1` (1-based) in order, given
- * g = G[S,S] (kb x kb, row-major, ld_g), the field row s (N int8, flipped in
- * place on accept), lambda, the Philox key/counter words. Writes Gamma (kb x kb,
- * row-major FP64) such that the accepted flips give
- *   G' = G - G[:,S] Gamma (I - G)[S,:]   (Woodbury form of the sequential
- *   Sherman-Morrison updates), and accept_count[0] (int). Non-positive or
- * non-finite ratios set *status = 1 and stop. forced != NULL (kb bytes)
- * replaces the Metropolis decision. */
+ * g = G[S,S] (kb x kb, row-major, ld_g, device FP64), the field row s (N int8,
+ * device, flipped in place on accept), lambda, the Philox key/counter words.
+ * Writes accept_count[0] = m and alpha, beta (kb x kb, row-major FP64, device):
+ * rows 0..m-1 hold the coefficient vectors of the accepted flips in order, the
+ * other rows zero, such that the m sequential Sherman-Morrison updates equal
+ *   G' = G - (G[:,S] alpha^T) (beta (E_S - G[S,:]))
+ * with E_S the kb x N selector of S. Non-positive or non-finite ratios set
+ * *status = 1 and stop. forced != NULL (kb bytes) replaces the decision. */
 dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, int ld_g,
                                      int8_t *s, double lambda, uint64_t seed, uint32_t chain,
                                      uint32_t sweep_pass, int slice1, const uint8_t *forced,
-                                     double *Gamma, int *accept_count, int *status, void *stream);
+                                     double *alpha, double *beta, int *accept_count, int *status,
+                                     void *stream);
 
-/* Rank-k flush: G <- G - Gcol * Gamma * (E_S - Grow), with Gcol = G[:,S]
- * (N x kb, ld kb) and Grow = G[S,:] (kb x N, ld N) taken before the update,
- * E_S the kb x N selector of S = [site0, site0+kb). G: N x N row-major FP64
- * (ldG = N). Gamma: kb x kb FP64. */
+/* Rank-m flush of one block: G <- G - (Gcol alpha^T)(beta (E_S - Grow)), with
+ * Gcol = G[:,S] (N x kb, ld kb) and Grow = G[S,:] (kb x N, ld N) taken before
+ * the update, alpha/beta/accept_count as written by dqmc_op_metropolis_block
+ * (device). G: N x N row-major (ld N), device. The N x kb factor A lives in
+ * scratch memory that the call allocates and frees on the stream.
+ * _f64: FP64 arithmetic; _df: FP64 storage, FP64-accurate double-float
+ * product on the FP32 units; _f32: FP32 G. */
 dqmc_status dqmc_op_flush_f64(int N, int site0, int kb, double *G, const double *Gcol,
-                              const double *Grow, const double *Gamma, void *stream);
+                              const double *Grow, const double *alpha, const double *beta,
+                              const int *accept_count, void *stream);
+dqmc_status dqmc_op_flush_df(int N, int site0, int kb, double *G, const double *Gcol,
+                             const double *Grow, const double *alpha, const double *beta,
+                             const int *accept_count, void *stream);
 dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *Gcol,
-                              const float *Grow, const double *Gamma, void *stream);
+                              const float *Grow, const double *alpha, const double *beta,
+                              const int *accept_count, void *stream);
+
+/* FP64 GEMM of the stabilisation, C = alpha op(A) op(B) + beta C (row-major,
+ * device), op = transpose when ta / tb. mode 0: FP64 FMA; 1: FP64-accurate
+ * double-float product on the FP32 units; 2: FP64-accurate product from exact
+ * 7-bit digit slices on the bf16 tensor cores (Ozaki-style error-free
+ * splitting; the stabilisation of the mixed precision mode uses it).
+ * Modes 1-2 allocate their operand workspace on the stream. */
+dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, double alpha,
+                             const double *A, int lda, const double *B, int ldb, double beta,
+                             double *C, int ldc, void *stream);
 
 /* Equal-time estimator sums from one FP64 G (N x N row-major, device): writes
  * out[6] (host) = S_pair_G, S_pair_dk, phi2_G, phi2_K, density, ekin, with the

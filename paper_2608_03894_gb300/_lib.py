@@ -59,10 +59,12 @@ SIGNATURES = {
     "dqmc_destroy": (None, [vp]),
     "dqmc_op_propagate_f64": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_propagate_f32": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
-    "dqmc_op_metropolis_block": (i32, [i32, i32, i32, vp, i32, vp, f64, u64, u32, u32, i32, vp, vp, vp, vp, vp]),
-    "dqmc_op_flush_f64": (i32, [i32, i32, i32, vp, vp, vp, vp, vp]),
-    "dqmc_op_flush_f32": (i32, [i32, i32, i32, vp, vp, vp, vp, vp]),
+    "dqmc_op_metropolis_block": (i32, [i32, i32, i32, vp, i32, vp, f64, u64, u32, u32, i32, vp, vp, vp, vp, vp, vp]),
+    "dqmc_op_flush_f64": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
+    "dqmc_op_flush_df": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
+    "dqmc_op_flush_f32": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_measure": (i32, [i32, vp, i32, vp, vp]),
+    "dqmc_op_gemm_f64": (i32, [i32, i32, i32, i32, i32, i32, f64, vp, i32, vp, i32, f64, vp, i32, vp]),
 }
 
 _lib = None

@@ -187,7 +187,14 @@ struct dqmc_ctx {
   double *ev64 = nullptr, *evi64 = nullptr;
   float *ev32 = nullptr, *evi32 = nullptr;
   void *Gcol[2] = {nullptr, nullptr}, *Grow[2] = {nullptr, nullptr};
-  double *Gamma = nullptr;
+  double *coef_a = nullptr, *coef_b = nullptr;  // K x K alpha / beta vectors of a block
+  void *Abuf = nullptr;                       // N x K rank-m factor A (or its FP32 pairs)
+  int df_flush = 1;   // mixed: rank-m flush as double-float product (else FP64)
+  int stab_gemm = 2;  // mixed: stabilisation GEMMs 0 FP64, 1 double-float, 2 tensor-core digit slices
+  unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
+  void *ozws = nullptr;  // digit-slice workspace
+  size_t ozws_bytes = 0;
+  int *ozexp = nullptr;
   int *acc = nullptr, *status = nullptr;
   unsigned long long *total_acc = nullptr;
   double *drift = nullptr, *drift_max = nullptr;
@@ -296,10 +303,15 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
   DQ_CHECK(ctx_alloc_n(c, &c->evi64, (size_t)N));
   DQ_CHECK(ctx_alloc_n(c, &c->ev32, (size_t)N));
   DQ_CHECK(ctx_alloc_n(c, &c->evi32, (size_t)N));
-  if (c->precision == 1) {
+  if (c->precision == 1 && c->stab_gemm == 1) {
     // split operands of the double-float GEMMs: at most M*K + K*N = 2 N^2 pairs
     c->dfws_elems = 2 * NN;
     DQ_CHECK(ctx_alloc_n(c, &c->dfws, c->dfws_elems));
+  }
+  if (c->precision == 1 && c->stab_gemm == 2) {
+    c->ozws_bytes = oz_workspace_bytes(N, N, N);
+    DQ_CHECK(ctx_alloc(c, &c->ozws, c->ozws_bytes));
+    DQ_CHECK(ctx_alloc_n(c, &c->ozexp, 2 * (size_t)N));
   }
   const size_t es = c->precision == 2 ? sizeof(float) : sizeof(double);
   for (int b = 0; b < 2; ++b) {
@@ -308,7 +320,9 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
     CK(cudaMemsetAsync(c->Gcol[b], 0, (size_t)N * c->k * es, c->stream));
     CK(cudaMemsetAsync(c->Grow[b], 0, (size_t)N * c->k * es, c->stream));
   }
-  DQ_CHECK(ctx_alloc_n(c, &c->Gamma, (size_t)c->k * c->k));
+  DQ_CHECK(ctx_alloc_n(c, &c->coef_a, (size_t)c->k * c->k));
+  DQ_CHECK(ctx_alloc_n(c, &c->coef_b, (size_t)c->k * c->k));
+  DQ_CHECK(ctx_alloc(c, &c->Abuf, (size_t)N * c->k * sizeof(double)));
   DQ_CHECK(ctx_alloc_n(c, &c->acc, 4));
   DQ_CHECK(ctx_alloc_n(c, &c->status, 4));
   DQ_CHECK(ctx_alloc_n(c, &c->total_acc, 1));
@@ -440,12 +454,8 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
   const int nblk = (N + K - 1) / K;
   T *Gc[2] = {static_cast<T *>(c->Gcol[0]), static_cast<T *>(c->Gcol[1])};
   T *Gr[2] = {static_cast<T *>(c->Grow[0]), static_cast<T *>(c->Grow[1])};
-  const bool df = (c->precision == 1);
-  if (df)
-    CK(launch_gather_df(N, 0, std::min(K, N), K, (const double *)G, (float2 *)c->Gcol[0],
-                        (double *)c->Grow[0], c->stream));
-  else
-    CK(launch_gather<T>(N, 0, std::min(K, N), K, G, Gc[0], Gr[0], c->stream));
+  const bool df = (c->precision == 1 && c->df_flush);
+  CK(launch_gather<T>(N, 0, std::min(K, N), K, G, Gc[0], Gr[0], c->stream));
   MetroArgs ma;
   ma.N = N;
   ma.K = K;
@@ -462,8 +472,8 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
     const int s0 = b * K, kb = std::min(K, N - s0);
     ma.s0 = s0;
     ma.kb = kb;
-    CK(launch_metropolis<T>(ma, Gr[b & 1] + s0, s, nullptr, c->Gamma, c->acc, c->status,
-                            c->total_acc, c->stream));
+    CK(launch_metropolis(ma, Gr[b & 1] + s0, sizeof(T) == 4, s, nullptr, c->coef_a, c->coef_b, c->acc,
+                         c->status, c->total_acc, c->stream));
     FlushArgs fa;
     fa.N = N;
     fa.s0 = s0;
@@ -472,13 +482,10 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
     fa.nkb = (b + 1 < nblk) ? std::min(K, N - s0 - K) : 0;
     fa.rows_per_cta = 0;
     fa.ldc = K;
-    if (df)
-      CK(launch_flush_df(K, fa, (double *)G, (const float2 *)c->Gcol[b & 1], (const double *)Gr[b & 1],
-                         c->Gamma, c->acc, (float2 *)c->Gcol[(b + 1) & 1], (double *)Gr[(b + 1) & 1],
-                         c->stream));
-    else
-      CK(launch_flush<T>(K, fa, G, Gc[b & 1], Gr[b & 1], c->Gamma, c->acc, Gc[(b + 1) & 1],
-                         Gr[(b + 1) & 1], c->stream));
+    fa.ldb = K;
+    fa.lda = K;
+    CK(launch_flush<T>(K, fa, G, Gc[b & 1], Gr[b & 1], c->coef_a, c->coef_b, c->acc, c->Abuf,
+                       Gc[(b + 1) & 1], Gr[(b + 1) & 1], df, c->stream));
   }
   c->proposed += N;
   return DQMC_OK;
@@ -509,10 +516,13 @@ dqmc_status udv_advance(dqmc_ctx *c, const UDVd &src, UDVd &dst, const std::vect
   CK(column_norms_scaled(c->X, N, src.D, c->norms, c->stream));
   CK(argsort_desc(c->norms, N, c->perm, c->stream));
   CK(permute_udv(c->X, src.D, src.T, c->perm, N, c->Xp, c->Dp, c->Tp, c->stream));
+  set_gemm_site(GS_QR_UPDATE);
   CK(qr_factor(c->Xp, N, c->qr, c->stream));
+  set_gemm_site(GS_FORM_Q);
   CK(qr_form_q(dst.U, N, c->qr, c->stream));
   CK(udv_diag_and_scale(c->Xp, N, c->Dp, dst.D, c->stream));
   // T_new = R'' (P^T T_old)
+  set_gemm_site(GS_T_UPDATE);
   CK(dgemm(false, false, N, N, N, 1.0, c->Xp, N, c->Tp, N, 0.0, dst.T, N, nullptr, nullptr, c->stream));
   return DQMC_OK;
 }
@@ -531,13 +541,19 @@ dqmc_status combine(dqmc_ctx *c, const UDVd &r, const UDVd &lf, double *Gout) {
   const int N = c->N;
   CK(split_scales(r.D, N, c->drmax_inv, c->drmin, c->stream));
   CK(split_scales(lf.D, N, c->dlmax_inv, c->dlmin, c->stream));
+  set_gemm_site(GS_UU);
   CK(dgemm(true, false, N, N, N, 1.0, r.U, N, lf.U, N, 0.0, c->Mm, N, c->drmax_inv, c->dlmax_inv, c->stream));
+  set_gemm_site(GS_TT);
   CK(dgemm(false, true, N, N, N, 1.0, r.T, N, lf.T, N, 1.0, c->Mm, N, c->drmin, c->dlmin, c->stream));
   CK(transpose_scale(r.U, N, c->Bm, N, c->drmax_inv, c->stream));
+  set_gemm_site(GS_QRM);
   CK(qr_factor(c->Mm, N, c->qr, c->stream));
+  set_gemm_site(GS_APPLY_QT);
   CK(qr_apply_qt(c->Bm, N, N, N, c->qr, c->stream));
+  set_gemm_site(GS_TRSM);
   CK(qr_solve_r(c->Mm, N, c->Bm, c->Z, N, c->qr, c->stream));
   CK(scale_rows_cols(c->Z, N, N, c->dlmax_inv, nullptr, c->stream));
+  set_gemm_site(GS_FINAL);
   CK(dgemm(false, false, N, N, N, 1.0, lf.U, N, c->Z, N, 0.0, Gout, N, nullptr, nullptr, c->stream));
   return DQMC_OK;
 }
@@ -561,16 +577,25 @@ __global__ void drift_max_kernel(const double *d, double *mx) {
   if (v != v || v > *mx) *mx = v;
 }
 
-// In mixed precision the stabilisation GEMMs of the sweep run as
-// FP64-accurate double-float products on the FP32 units.
+// In mixed precision the stabilisation GEMMs of the sweep run FP64-accurate
+// on faster units: digit slices on the bf16 tensor cores (default) or
+// double-float products on the FP32 units.
 struct GemmModeScope {
   explicit GemmModeScope(dqmc_ctx *c) {
-    if (c->precision == 1 && c->dfws) {
+    if (c->precision != 1) return;
+    if (c->stab_gemm == 1 && c->dfws) {
       set_df_workspace(c->dfws, c->dfws_elems);
       set_gemm_df(true);
+    } else if (c->stab_gemm == 2 && c->ozws) {
+      set_oz_workspace(c->ozws, c->ozws_bytes, c->ozexp, 2 * (size_t)c->N);
+      set_gemm_oz(true);
     }
+    set_gemm_site_mask(c->gemm_sites);
   }
-  ~GemmModeScope() { set_gemm_df(false); }
+  ~GemmModeScope() {
+    set_gemm_df(false);
+    set_gemm_oz(false);
+  }
 };
 
 dqmc_status ensure_ready(dqmc_ctx *c) {
@@ -836,6 +861,16 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) {
   } else if (k == "bin") {
     if (v < 1) return fail(DQMC_EINVAL, "bin must be >= 1");
     c->bin = (int)v;
+  } else if (k == "df_flush") {
+    if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
+    c->df_flush = v != 0.0;
+  } else if (k == "gemm_sites") {
+    if (v < 0 || v > 4294967295.0) return fail(DQMC_EINVAL, "gemm_sites is a 32-bit mask");
+    c->gemm_sites = (unsigned)v;
+  } else if (k == "stab_gemm") {
+    if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
+    if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "stab_gemm must be 0, 1 or 2");
+    c->stab_gemm = (int)v;
   } else if (k == "drift_limit") {
     if (!(v > 0.0)) return fail(DQMC_EINVAL, "drift_limit must be positive");
     c->drift_limit = v;
@@ -897,15 +932,14 @@ dqmc_status dqmc_green(dqmc_ctx *c, int slice, double *G_out) {
   DQ_CHECK(ensure_ready(c));
   // right chain B(slice, 0) in tmpA, left chain B(beta, slice)^T in tmpB, QR every n_stab slices
   DQ_CHECK(udv_identity(c, c->tmpA));
-  for (int l0 = 0; l0 < slice; l0 += c->n_stab) {
-    std::vector<int> sl;
-    for (int m = l0 + 1; m <= std::min(slice, l0 + c->n_stab); ++m) sl.push_back(m);
+  // reference-quality chains: a pivoted QR after every slice
+  for (int l0 = 0; l0 < slice; ++l0) {
+    std::vector<int> sl{l0 + 1};
     DQ_CHECK(udv_advance(c, c->tmpA, c->tmpA, sl, false));
   }
   DQ_CHECK(udv_identity(c, c->tmpB));
-  for (int l1 = c->M; l1 > slice; l1 -= c->n_stab) {
-    std::vector<int> sl;
-    for (int m = l1; m > std::max(slice, l1 - c->n_stab); --m) sl.push_back(m);
+  for (int l1 = c->M; l1 > slice; --l1) {
+    std::vector<int> sl{l1};
     DQ_CHECK(udv_advance(c, c->tmpB, c->tmpB, sl, true));
   }
   DQ_CHECK(combine(c, c->tmpA, c->tmpB, c->Xp));

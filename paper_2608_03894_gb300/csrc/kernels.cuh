@@ -19,6 +19,9 @@ template <typename T>
 cudaError_t launch_gather(int N, int s0, int kb, int K, const T *G, T *Gcol, T *Grow,
                           cudaStream_t st);
 
+// One delayed-update block: decisions, flips in s, and the coefficient
+// vectors alpha (rows m' < m, row stride K) and beta of the accepted flips;
+// g = G[S,S] (double, or float when g_f32).
 struct MetroArgs {
   int N, s0, kb, K;
   int ld_g;              // row stride of g = G[S, S]
@@ -27,28 +30,25 @@ struct MetroArgs {
   uint32_t c2, c3;       // counter words 2 (2*sweep + pass) and 3 (chain | domain << 24)
   int slice0;            // counter word 1 (0-based slice)
 };
-template <typename TG>
-cudaError_t launch_metropolis(const MetroArgs &a, const TG *g, int8_t *s, const uint8_t *forced,
-                              double *Gamma, int *accept_count, int *status,
-                              unsigned long long *total, cudaStream_t st);
+cudaError_t launch_metropolis(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
+                              const uint8_t *forced, double *alpha, double *beta, int *accept_count,
+                              int *status, unsigned long long *total, cudaStream_t st);
 
 struct FlushArgs {
   int N, s0, kb;   // current block
   int ns0, nkb;    // next block (nkb = 0: none)
   int rows_per_cta;
   int ldc;         // row stride of Gcol (>= kb); the next-block Gcol uses stride K
+  int ldb;         // row stride of beta
+  int lda;         // row stride of alpha
 };
+// G <- G - (Gcol alpha^T)(beta (E_S - Grow)): the A kernel then the rank-m
+// flush. Abuf: N x K scratch (T, or float2 pairs when df). df = FP64-accurate
+// double-float product on the FP32 units (T = double only).
 template <typename T>
 cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
-                         const double *Gamma, const int *acc, T *Gcol_next, T *Grow_next,
-                         cudaStream_t st);
-// FP64-accurate flush on the FP32 units: G and Grow FP64, Gcol as (hi, lo)
-// FP32 pairs (stride K, zero beyond kb), next-block Gcol written split.
-cudaError_t launch_flush_df(int K, const FlushArgs &a, double *G, const float2 *Gcol,
-                            const double *Grow, const double *Gamma, const int *acc,
-                            float2 *Gcol_next, double *Grow_next, cudaStream_t st);
-cudaError_t launch_gather_df(int N, int s0, int kb, int K, const double *G, float2 *Gcol,
-                             double *Grow, cudaStream_t st);
+                         const double *alpha, const double *beta, const int *acc, void *Abuf,
+                         T *Gcol_next, T *Grow_next, bool df, cudaStream_t st);
 
 // ---- measurement (measure.cu)
 struct MeasTables {

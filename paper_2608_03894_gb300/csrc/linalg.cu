@@ -121,6 +121,11 @@ static int grid_for(long work, int per = 256) {
   return (int)g;
 }
 
+static thread_local int t_site = 0;
+static thread_local unsigned t_site_mask = 0xffffffffu;
+void set_gemm_site(int site) { t_site = site; }
+void set_gemm_site_mask(unsigned mask) { t_site_mask = mask; }
+
 cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st) {
   DQ_KSCOPE(KF_OTHER, st);
   scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
@@ -131,7 +136,10 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
                   const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
                   const double *cs, cudaStream_t st, int splitk) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (K > 0 && gemm_df())
+  const bool fast_site = (t_site_mask >> t_site) & 1u;
+  if (K > 0 && fast_site && gemm_oz())
+    return ozgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, st);
+  if (K > 0 && fast_site && gemm_df())
     return dfgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, st, splitk, 304);
   if (K <= 0) {
     DQ_KSCOPE(KF_OTHER, st);

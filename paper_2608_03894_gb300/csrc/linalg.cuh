@@ -21,6 +21,36 @@ cudaError_t dfgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
 void set_df_workspace(float2 *ws, size_t elems);  // >= max over calls of M*K + K*N pairs
 void set_gemm_df(bool on);
 bool gemm_df();
+
+// FP64-accurate GEMM from exact 7-bit digit slices on the bf16 tensor cores
+// (see ozgemm.cu). While set_gemm_oz(true) is in effect for the calling thread
+// (and a workspace is bound), dgemm runs as ozgemm.
+cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
+                   const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
+                   const double *cs, cudaStream_t st);
+size_t oz_workspace_bytes(int M, int N, int K);
+void set_oz_workspace(void *ws, size_t bytes, int *exps, size_t nexp);  // exps: >= M + N ints
+void set_gemm_oz(bool on);
+bool gemm_oz();
+
+// Call sites of the stabilisation GEMMs. The fast FP64-accurate variants
+// (double-float, digit slices) are accurate relative to the largest entries
+// of a row / column, not per term; the mask selects the sites where they are
+// used (bit s = site s), the others stay FP64 FMA.
+enum GemmSite {
+  GS_QR_UPDATE = 0,  // trailing update of a Householder QR
+  GS_FORM_Q,         // explicit Q
+  GS_T_UPDATE,       // T_new = R'' P^T T_old (graded R'')
+  GS_UU,             // U_r^T U_l
+  GS_TT,             // T_r T_l^T
+  GS_QRM,            // trailing updates of the QR of the scale-separated matrix
+  GS_APPLY_QT,       // Q^T B in the solve
+  GS_TRSM,           // block triangular solve
+  GS_FINAL,          // G = U_l Z
+  GS_COUNT
+};
+void set_gemm_site(int site);
+void set_gemm_site_mask(unsigned mask);
 cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st);
 
 // Householder QR workspace for an n x n matrix: V (unit lower trapezoidal,

@@ -9,6 +9,7 @@
 
 #include "kernels.cuh"
 #include "lattice_host.h"
+#include "linalg.cuh"
 
 namespace dq {
 
@@ -85,10 +86,11 @@ dqmc_status dqmc_op_propagate_f32(int L, double scale, int side, const float *X,
 dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, int ld_g,
                                      int8_t *s, double lambda, uint64_t seed, uint32_t chain,
                                      uint32_t sweep_pass, int slice1, const uint8_t *forced,
-                                     double *Gamma, int *accept_count, int *status, void *stream) {
+                                     double *alpha, double *beta, int *accept_count, int *status,
+                                     void *stream) {
   if (N < 1 || kb < 1 || kb > 64 || site0 < 0 || site0 + kb > N)
     return fail(DQMC_EINVAL, "need 1 <= kb <= 64 and 0 <= site0, site0 + kb <= N");
-  if (!g || !s || !Gamma || !accept_count || !status) return fail(DQMC_EINVAL, "null pointer");
+  if (!g || !s || !alpha || !beta || !accept_count || !status) return fail(DQMC_EINVAL, "null pointer");
   if (ld_g < kb) return fail(DQMC_EINVAL, "ld_g < kb");
   if (!(lambda >= 0.0)) return fail(DQMC_EINVAL, "lambda must be >= 0");
   if (slice1 < 1) return fail(DQMC_EINVAL, "slice1 is 1-based");
@@ -105,8 +107,8 @@ dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, 
   a.c2 = sweep_pass;
   a.c3 = (chain & 0xffffffu) | (kDomainMetropolis << 24);
   a.slice0 = slice1 - 1;
-  DQ_CUDA(launch_metropolis<double>(a, g, s, forced, Gamma, accept_count, status, nullptr,
-                                    static_cast<cudaStream_t>(stream)));
+  DQ_CUDA(launch_metropolis(a, g, false, s, forced, alpha, beta, accept_count, status, nullptr,
+                            static_cast<cudaStream_t>(stream)));
   return DQMC_OK;
 }
 
@@ -114,28 +116,77 @@ dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, 
 
 template <typename T>
 static dqmc_status op_flush(int N, int site0, int kb, T *G, const T *Gcol, const T *Grow,
-                            const double *Gamma, void *stream) {
+                            const double *alpha, const double *beta, const int *accept_count,
+                            bool df, void *stream) {
   if (N < 1 || kb < 1 || kb > 64 || site0 < 0 || site0 + kb > N)
     return fail(DQMC_EINVAL, "need 1 <= kb <= 64 and 0 <= site0, site0 + kb <= N");
-  if (!G || !Gcol || !Grow || !Gamma) return fail(DQMC_EINVAL, "null pointer");
+  if (!G || !Gcol || !Grow || !alpha || !beta || !accept_count) return fail(DQMC_EINVAL, "null pointer");
   int K = 4;
   while (K < kb) K <<= 1;
-  FlushArgs a{N, site0, kb, 0, 0, 0, kb};
-  DQ_CUDA(launch_flush<T>(K, a, G, Gcol, Grow, Gamma, nullptr, nullptr, nullptr,
-                          static_cast<cudaStream_t>(stream)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // scratch for the N x K factor A, stream-ordered
+  void *Abuf = nullptr;
+  DQ_CUDA(cudaMallocAsync(&Abuf, (size_t)N * K * 8, st));
+  FlushArgs a{N, site0, kb, 0, 0, 0, kb, kb, kb};
+  cudaError_t e = launch_flush<T>(K, a, G, Gcol, Grow, alpha, beta, accept_count, Abuf, nullptr,
+                                  nullptr, df, st);
+  cudaError_t e2 = cudaFreeAsync(Abuf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "flush");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
   return DQMC_OK;
 }
 
 extern "C" {
 
 dqmc_status dqmc_op_flush_f64(int N, int site0, int kb, double *G, const double *Gcol,
-                              const double *Grow, const double *Gamma, void *stream) {
-  return op_flush<double>(N, site0, kb, G, Gcol, Grow, Gamma, stream);
+                              const double *Grow, const double *alpha, const double *beta,
+                              const int *accept_count, void *stream) {
+  return op_flush<double>(N, site0, kb, G, Gcol, Grow, alpha, beta, accept_count, false, stream);
+}
+
+dqmc_status dqmc_op_flush_df(int N, int site0, int kb, double *G, const double *Gcol,
+                             const double *Grow, const double *alpha, const double *beta,
+                             const int *accept_count, void *stream) {
+  return op_flush<double>(N, site0, kb, G, Gcol, Grow, alpha, beta, accept_count, true, stream);
 }
 
 dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *Gcol,
-                              const float *Grow, const double *Gamma, void *stream) {
-  return op_flush<float>(N, site0, kb, G, Gcol, Grow, Gamma, stream);
+                              const float *Grow, const double *alpha, const double *beta,
+                              const int *accept_count, void *stream) {
+  return op_flush<float>(N, site0, kb, G, Gcol, Grow, alpha, beta, accept_count, false, stream);
+}
+
+dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, double alpha,
+                             const double *A, int lda, const double *B, int ldb, double beta,
+                             double *C, int ldc, void *stream) {
+  if (mode < 0 || mode > 2) return fail(DQMC_EINVAL, "mode must be 0 (FP64), 1 (double-float) or 2 (digit slices)");
+  if (M < 0 || N < 0 || K < 0) return fail(DQMC_EINVAL, "negative size");
+  if ((M && N && K) && (!A || !B)) return fail(DQMC_EINVAL, "null operand");
+  if (M && N && !C) return fail(DQMC_EINVAL, "null C");
+  if (lda < (ta ? M : K) || ldb < (tb ? K : N) || ldc < N) return fail(DQMC_EINVAL, "leading dimension too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *ws = nullptr;
+  int *ex = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (mode == 1) {
+    DQ_CUDA(cudaMallocAsync(&ws, ((size_t)M * K + (size_t)K * N + 1) * sizeof(float2), st));
+    set_df_workspace(static_cast<float2 *>(ws), (size_t)M * K + (size_t)K * N + 1);
+    e = dfgemm(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, nullptr, st, 0, 304);
+    set_df_workspace(nullptr, 0);
+  } else if (mode == 2) {
+    const size_t bytes = oz_workspace_bytes(M, N, K) + 16;
+    DQ_CUDA(cudaMallocAsync(&ws, bytes, st));
+    DQ_CUDA(cudaMallocAsync((void **)&ex, ((size_t)M + N + 1) * sizeof(int), st));
+    set_oz_workspace(ws, bytes, ex, (size_t)M + N + 1);
+    e = ozgemm(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, nullptr, st);
+    set_oz_workspace(nullptr, 0, nullptr, 0);
+  } else {
+    e = dgemm(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, nullptr, st);
+  }
+  if (ws) cudaFreeAsync(ws, st);
+  if (ex) cudaFreeAsync(ex, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gemm");
+  return DQMC_OK;
 }
 
 dqmc_status dqmc_op_measure(int L, const double *G, int site_offsets, double *out, void *stream) {

@@ -1,0 +1,321 @@
+// FP64-accurate GEMM on the bf16 tensor cores by exact slicing (the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012).
+//
+// op(A) (M x K) and op(B) (K x N) are scaled per row / per column by powers of
+// two, E_i and F_j, so that every entry lies in (-1, 1), and each entry is cut
+// into 9 signed 7-bit digits:  a = 2^E_i sum_{p=1..9} a_p 2^{-7p} (+ a tail
+// below 2^-63), a_p integers in [-127, 127], exactly representable in bf16.
+// Then
+//     (op(A) op(B))_ij = 2^{E_i+F_j} sum_{p,q} 2^{-7(p+q)} sum_k a_p[i,k] b_q[k,j],
+// keeping the 45 digit pairs with p + q <= 10 (the dropped ones, and the
+// truncated tails, weigh less than about K 2^-63 max|row| max|column|: FP64
+// rounding level for K up to a few thousand). Each inner sum over a K-chunk
+// of 64 is a sum of products of 7-bit integers, < 9 * 64 * 127^2 < 2^24 per
+// level, so the bf16 tensor-core MMA with FP32 accumulation computes it
+// exactly. Levels l = p + q in 2..7 fold into one exact int64 accumulator
+// (weights 2^{7(7-l)}), levels 8..10 into an FP32 accumulator; the FP64
+// result is formed once per output.
+//
+// Tensor path: legacy warp-level mma.sync m16n8k16 bf16 (measured 0.6 PFLOP/s
+// on this part); a tcgen05/TMEM version would be the next step.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "linalg.cuh"
+
+namespace dq {
+
+constexpr int OZ_S = 9;       // digits per value (63 bits)
+constexpr int OZ_KC = 64;      // K chunk
+constexpr int OZ_BM = 64, OZ_BN = 64;
+constexpr int OZ_LD = OZ_KC + 8;  // padded smem row (bf16): 144 B, conflict-free ldmatrix
+
+// exponent field (biased) of |x|; 0 for zero / subnormal
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// Per-row (rows of op(A)) or per-column (columns of op(B)) maximum exponent
+// field. Elements are visited in storage order; `vec_of_row` says whether the
+// storage row index or the storage column index is the vector index.
+__global__ void oz_maxexp_kernel(const double *__restrict__ X, int rows, int cols, int ld,
+                                 int vec_is_row, int *__restrict__ emax) {
+  const long total = (long)rows * cols;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), c = (int)(e % cols);
+    const int ex = exp_field(X[(size_t)r * ld + c]);
+    atomicMax(&emax[vec_is_row ? r : c], ex);
+  }
+}
+
+__device__ __forceinline__ unsigned short int_to_bf16_bits(int d) {
+  if (d == 0) return 0;
+  const unsigned int s = d < 0 ? 0x8000u : 0u;
+  const unsigned int a = (unsigned int)(d < 0 ? -d : d);   // 1..127
+  const int msb = 31 - __clz(a);                             // 0..6
+  const unsigned int mant = (a << (7 - msb)) & 0x7f;         // 7 mantissa bits, exact
+  return (unsigned short)(s | ((unsigned int)(msb + 127) << 7) | mant);
+}
+
+// Digits of element (v, k) of the vectors (rows of op(A) / columns of op(B)),
+// written to out[p][v][k] (bf16, row length Kp, zero padded); the vector's
+// exponent is emax[v]. Integer operations only.
+__global__ void oz_slice_kernel(const double *__restrict__ X, int rows, int cols, int ld,
+                                int vec_is_row, const int *__restrict__ emax, int nvec, int Kp,
+                                unsigned short *__restrict__ out) {
+  const long total = (long)nvec * Kp;
+  const size_t plane = (size_t)nvec * Kp;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int v = (int)(e / Kp), k = (int)(e % Kp);
+    double x = 0.0;
+    const int K = vec_is_row ? cols : rows;
+    if (k < K) x = vec_is_row ? X[(size_t)v * ld + k] : X[(size_t)k * ld + v];
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((b >> 52) & 0x7ff);
+    unsigned long long F = 0;
+    if (ef != 0 && ef != 0x7ff) {
+      const unsigned long long m53 = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      // |x| / 2^{E} with E = emax - 1022 as a fixed-point number with 7 S = 63
+      // fraction bits (m53 < 2^53, shift <= 10)
+      const int sh = ef - emax[v] + (7 * OZ_S - 53);
+      F = sh >= 0 ? (m53 << sh) : (sh > -64 ? (m53 >> (-sh)) : 0ull);
+    }
+    const int neg = (int)(b >> 63);
+#pragma unroll
+    for (int p = 1; p <= OZ_S; ++p) {
+      int d = (int)((F >> (7 * OZ_S - 7 * p)) & 127ull);
+      if (neg) d = -d;
+      out[(size_t)(p - 1) * plane + (size_t)v * Kp + k] = int_to_bf16_bits(d);
+    }
+  }
+}
+
+__device__ __forceinline__ void ldmatrix_x4(unsigned (&r)[4], const void *p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C = alpha diag(rs) (op(A) op(B)) diag(cs) + beta C from the digit planes.
+// CTA tile 64 x 64, 8 warps (warp tile 16 x 32 = 4 MMA n-tiles). Per K chunk
+// all 8 digit planes of the A and B tiles are staged in shared memory; the
+// level loop keeps one FP32 accumulator live.
+__global__ void __launch_bounds__(256)
+    oz_gemm_kernel(int M, int N, int Kp, const unsigned short *__restrict__ Ad,
+                   const unsigned short *__restrict__ Bd, const int *__restrict__ ea,
+                   const int *__restrict__ eb, double alpha, double beta, double *__restrict__ C,
+                   int ldc, const double *__restrict__ rs, const double *__restrict__ cs, int kchunks,
+                   int atomic) {
+  extern __shared__ __align__(16) unsigned short osm[];
+  unsigned short *As = osm;                              // [p][64][OZ_LD]
+  unsigned short *Bs = osm + OZ_S * OZ_BM * OZ_LD;       // [q][64 (n)][OZ_LD]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;               // 4 x 2 warps
+  const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
+  const size_t aplane = (size_t)M * Kp, bplane = (size_t)N * Kp;
+
+  long long I[4][4];
+  float F[4][4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      I[t][r] = 0;
+      F[t][r] = 0.f;
+    }
+
+  // split K: this CTA takes chunks [z * kchunks, (z + 1) * kchunks)
+  const int kbeg = blockIdx.z * kchunks * OZ_KC;
+  const int kend = min(Kp, kbeg + kchunks * OZ_KC);
+  for (int k0 = kbeg; k0 < kend; k0 += OZ_KC) {
+    // stage 8 planes of A (64 x 64) and B (64 x 64): 16-byte copies
+    for (int e = tid; e < OZ_S * OZ_BM * (OZ_KC / 8); e += 256) {
+      const int p = e / (OZ_BM * (OZ_KC / 8));
+      const int rem = e % (OZ_BM * (OZ_KC / 8));
+      const int r = rem / (OZ_KC / 8), c8 = rem % (OZ_KC / 8);
+      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+      if (m0 + r < M) va = *reinterpret_cast<const uint4 *>(Ad + p * aplane + (size_t)(m0 + r) * Kp + k0 + c8 * 8);
+      if (n0 + r < N) vb = *reinterpret_cast<const uint4 *>(Bd + p * bplane + (size_t)(n0 + r) * Kp + k0 + c8 * 8);
+      *reinterpret_cast<uint4 *>(As + (p * OZ_BM + r) * OZ_LD + c8 * 8) = va;
+      *reinterpret_cast<uint4 *>(Bs + (p * OZ_BN + r) * OZ_LD + c8 * 8) = vb;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int l = 2; l <= OZ_S + 1; ++l) {
+      float acc[4][4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[t][r] = 0.f;
+      const int plo = l - OZ_S > 1 ? l - OZ_S : 1, phi = l - 1 < OZ_S ? l - 1 : OZ_S;
+#pragma unroll 1
+      for (int p = plo; p <= phi; ++p) {
+        const int q = l - p;
+        const unsigned short *Ap = As + ((p - 1) * OZ_BM + wm * 16) * OZ_LD;
+        const unsigned short *Bq = Bs + ((q - 1) * OZ_BN + wn * 32) * OZ_LD;
+#pragma unroll
+        for (int ks = 0; ks < OZ_KC; ks += 16) {
+          unsigned a[4];
+          ldmatrix_x4(a, Ap + (lane & 15) * OZ_LD + ks + (lane >> 4) * 8);
+#pragma unroll
+          for (int t2 = 0; t2 < 2; ++t2) {  // two pairs of n-tiles
+            unsigned b[4];
+            const int nrow = t2 * 16 + ((lane >> 4) << 3) + (lane & 7);
+            const int kof = ((lane >> 3) & 1) * 8;
+            ldmatrix_x4(b, Bq + nrow * OZ_LD + ks + kof);
+            mma_bf16(acc[2 * t2], a, b[0], b[1]);
+            mma_bf16(acc[2 * t2 + 1], a, b[2], b[3]);
+          }
+        }
+      }
+      // fold the exact level sums: levels 2..7 into the int64 accumulator
+      // (weight 2^{7(7-l)}; per chunk < 2^55, over <= 256 chunks < 2^63),
+      // levels 8..10 into FP32 (their rounding is below 2^-58 of the result)
+      if (l <= 7) {
+        const int shift = 7 * (7 - l);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) I[t][r] += ((long long)__float2int_rn(acc[t][r])) << shift;
+      } else {
+        const float w = __int_as_float((127 - 7 * (l - 7)) << 23);  // 2^{-7(l-7)}
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) F[t][r] = fmaf(acc[t][r], w, F[t][r]);
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: value = (I + F) 2^{-49} 2^{E_i + F_j}, E = emax - 1022
+  const int g = lane >> 2, c2 = (lane & 3) * 2;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = m0 + wm * 16 + g + ((r >> 1) << 3);
+      const int j = n0 + wn * 32 + t * 8 + c2 + (r & 1);
+      if (i >= M || j >= N) continue;
+      const double dot = ((double)I[t][r] + (double)F[t][r]);
+      const int e2 = (ea[i] - 1022) + (eb[j] - 1022) - 49;
+      double v = ldexp(dot, e2) * alpha;
+      if (rs) v *= rs[i];
+      if (cs) v *= cs[j];
+      double *cp = C + (size_t)i * ldc + j;
+      if (atomic)
+        atomicAdd(cp, v);
+      else
+        *cp = (beta != 0.0) ? v + beta * (*cp) : v;
+    }
+}
+
+static thread_local unsigned short *t_ozws = nullptr;
+static thread_local size_t t_ozws_bytes = 0;
+static thread_local int *t_ozexp = nullptr;
+static thread_local size_t t_ozexp_n = 0;
+static thread_local bool t_oz = false;
+
+void set_gemm_oz(bool on) { t_oz = on; }
+bool gemm_oz() { return t_oz && t_ozws != nullptr; }
+
+void set_oz_workspace(void *ws, size_t bytes, int *exps, size_t nexp) {
+  t_ozws = static_cast<unsigned short *>(ws);
+  t_ozws_bytes = bytes;
+  t_ozexp = exps;
+  t_ozexp_n = nexp;
+}
+
+size_t oz_workspace_bytes(int M, int N, int K) {
+  const size_t Kp = (size_t)((K + OZ_KC - 1) / OZ_KC) * OZ_KC;
+  return (size_t)OZ_S * ((size_t)M + N) * Kp * sizeof(unsigned short);
+}
+
+static int oz_grid(long work) {
+  long g = (work + 255) / 256;
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
+                   const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
+                   const double *cs, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const int Kp = ((K + OZ_KC - 1) / OZ_KC) * OZ_KC;
+  if (oz_workspace_bytes(M, N, K) > t_ozws_bytes || (size_t)(M + N) > t_ozexp_n)
+    return cudaErrorInvalidValue;
+  unsigned short *Ad = t_ozws, *Bd = t_ozws + (size_t)OZ_S * M * Kp;
+  int *ea = t_ozexp, *eb = t_ozexp + M;
+  cudaError_t e = cudaMemsetAsync(t_ozexp, 0, (size_t)(M + N) * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  {
+    DQ_KSCOPE(KF_OTHER, st);
+    // op(A) rows: storage rows when !ta; storage columns when ta
+    if (!ta)
+      oz_maxexp_kernel<<<oz_grid((long)M * K), 256, 0, st>>>(A, M, K, lda, 1, ea);
+    else
+      oz_maxexp_kernel<<<oz_grid((long)M * K), 256, 0, st>>>(A, K, M, lda, 0, ea);
+  }
+  {
+    DQ_KSCOPE(KF_OTHER, st);
+    // op(B) columns: storage columns when !tb; storage rows when tb
+    if (!tb)
+      oz_maxexp_kernel<<<oz_grid((long)K * N), 256, 0, st>>>(B, K, N, ldb, 0, eb);
+    else
+      oz_maxexp_kernel<<<oz_grid((long)K * N), 256, 0, st>>>(B, N, K, ldb, 1, eb);
+  }
+  {
+    DQ_KSCOPE(KF_OTHER, st);
+    if (!ta)
+      oz_slice_kernel<<<oz_grid((long)M * Kp), 256, 0, st>>>(A, M, K, lda, 1, ea, M, Kp, Ad);
+    else
+      oz_slice_kernel<<<oz_grid((long)M * Kp), 256, 0, st>>>(A, K, M, lda, 0, ea, M, Kp, Ad);
+  }
+  {
+    DQ_KSCOPE(KF_OTHER, st);
+    if (!tb)
+      oz_slice_kernel<<<oz_grid((long)N * Kp), 256, 0, st>>>(B, K, N, ldb, 0, eb, N, Kp, Bd);
+    else
+      oz_slice_kernel<<<oz_grid((long)N * Kp), 256, 0, st>>>(B, N, K, ldb, 1, eb, N, Kp, Bd);
+  }
+  const int smem = 2 * OZ_S * OZ_BM * OZ_LD * (int)sizeof(unsigned short);
+  e = ensure_smem_attr((const void *)oz_gemm_kernel, smem);
+  if (e != cudaSuccess) return e;
+  // one CTA per SM (shared memory); split K when the tiles do not fill the GPU
+  const int tiles = ((N + OZ_BN - 1) / OZ_BN) * ((M + OZ_BM - 1) / OZ_BM);
+  const int nchunks = Kp / OZ_KC;
+  int splits = 1;
+  if (tiles < 152) {
+    splits = (152 + tiles - 1) / tiles;
+    const int maxs = (nchunks + 1) / 2;  // at least two chunks per split
+    if (splits > maxs) splits = maxs;
+    if (splits < 1) splits = 1;
+  }
+  const int kchunks = (nchunks + splits - 1) / splits;
+  splits = (nchunks + kchunks - 1) / kchunks;
+  const int atomic = splits > 1;
+  if (atomic) {
+    e = scale_matrix(C, M, N, ldc, beta, st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((N + OZ_BN - 1) / OZ_BN, (M + OZ_BM - 1) / OZ_BM, splits);
+  DQ_KSCOPE(KF_GEMM, st);
+  add_work(KF_GEMM, 2.0 * M * (double)N * K,
+           8.0 * ((double)M * K + (double)K * N + (beta != 0.0 ? 2.0 : 1.0) * (double)M * N));
+  oz_gemm_kernel<<<grid, 256, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
+                                          kchunks, atomic);
+  return cudaGetLastError();
+}
+
+}  // namespace dq

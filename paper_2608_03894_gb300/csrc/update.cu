@@ -1,20 +1,65 @@
 // Delayed-update Metropolis over one time slice.
 //
 // Sites are proposed in index order in blocks S of k consecutive sites. For a
-// block, every quantity the sequential Sherman-Morrison updates need lies in
-// the k x k sub-block g = G[S,S] (submatrix form of the delayed update): the
-// current diagonal G~_jj, the restricted columns/rows of the accepted updates,
-// and two coefficient recursions alpha, beta such that after the block
-//     G' = G - G[:,S] Gamma (I - G)[S,:],   Gamma = sum_m alpha_m beta_m^T,
-// which is exactly the product of the sequential rank-one updates (Woodbury).
-// The block's serial loop runs in one CTA in FP64 (ratios and bookkeeping);
-// the flush is one rank-k product over the whole N x N G in the working
-// precision, and its epilogue gathers G[:,S'] and G[S',:] of the next block.
+// block, everything the sequential Sherman-Morrison updates need lies in the
+// k x k sub-block g = G[S,S] (submatrix form of the delayed update): the
+// current diagonal G~_jj and, per accepted flip m at block site t_m, the
+// restricted update column As_m = (delta/r) G~[S, t_m] and row
+// Bs_m = e_t - G~[t_m, S]. Two coefficient recursions alpha_m, beta_m in R^k,
+//     alpha_m = c_m (e_t - sum_{m'<m} alpha_m' Bs_m'[t]),
+//     beta_m  = e_t + sum_{m'<m} As_m'[t] beta_m',
+// give the full-space updates a_m = G[:,S] alpha_m and
+// b_m^T = beta_m^T (E_S - G[S,:]), so that after the block
+//     G' = G - A B^T,  A = G[:,S] [alpha_0 .. alpha_{m-1}],  B^T = [beta_m] (E_S - G[S,:]),
+// which equals the sequential rank-one updates exactly (Woodbury form with
+// Gamma = sum alpha beta^T never formed). The flush is a rank-m update with
+// m the number of accepted flips.
+//
+// Per block: metropolis (1 CTA, FP64), A = G[:,S] alpha (N x m, FP64), flush
+// (one CTA per 4-column stripe; B formed per stripe) whose epilogue gathers
+// G[:,S'] and G[S',:] of the next block.
 #include <type_traits>
 
 #include "kernels.cuh"
 
 namespace dq {
+
+// ----------------------------------------------------------------- FP64 <-> FP32 pairs
+// Split x into hi + lo (FP32) with integer operations only (the FP64 pipe is
+// 1/64 of the FP32 rate on GB300): hi carries the top 24 significand bits of
+// x (truncated), lo the next 24 of the remaining 29 (rounded by the integer
+// to FP32 conversion): |x - hi - lo| <= 2^-47 |x|. Values outside the FP32
+// normal range map to 0 (|x| < 2^-126) or +-inf.
+__device__ __forceinline__ float2 split_df_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  const int e32 = e - 1023 + 127;
+  if (e32 <= 0) return make_float2(0.f, 0.f);
+  if (e32 >= 255) return make_float2(__int_as_float(sign | 0x7f800000u), 0.f);
+  const float hi = __int_as_float(sign | ((unsigned int)e32 << 23) | (unsigned int)(mant >> 29));
+  const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull);  // 29 bits, weight 2^(e-1075)
+  const int el = e - 1075 + 127;                                 // FP32 exponent of 2^(e-1075)
+  float lo = 0.f;
+  if (rem != 0u && el > 0) {
+    lo = __uint2float_rn(rem) * __int_as_float((unsigned int)el << 23);
+    if (sign) lo = -lo;
+  }
+  return make_float2(hi, lo);
+}
+
+// FP32 -> FP64 by re-biasing the exponent (integer operations only); FP32
+// subnormals map to 0.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int b = (unsigned int)__float_as_int(f);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned int e = (b >> 23) & 0xff;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long e11 = (e == 255) ? 2047ull : (unsigned long long)(e + 896);
+  const unsigned long long mant = (unsigned long long)(b & 0x7fffff) << 29;
+  return __longlong_as_double((long long)(sign | (e11 << 52) | mant));
+}
 
 // ----------------------------------------------------------------- gather
 // Gcol[i*K + t] = G[i, s0 + t] (t < kb, zero for kb <= t < K),
@@ -53,60 +98,75 @@ template cudaError_t launch_gather<float>(int, int, int, int, const float *, flo
                                           cudaStream_t);
 
 // ----------------------------------------------------------------- Metropolis block
-
-// One CTA of K threads (K = 32 or 64 rounded up from kb). Thread u owns
-// block-local site u. Shared: g (kb x (kb+1)), and per accepted flip m the
-// restricted update column As[m][*] = (delta/r) G~[S, j], row
-// Bs[m][*] = e_j - G~[j, S], and the coefficient vectors al[m][*], be[m][*].
-template <typename TG>
-__global__ void metropolis_block_kernel(MetroArgs a, const TG *__restrict__ g, int8_t *s,
-                                        const uint8_t *__restrict__ forced, double *Gamma,
-                                        int *accept_count, int *status,
-                                        unsigned long long *total) {
+// One CTA of 4 warps. Lane u of every warp owns block sites u and u + 32.
+// On an accepted flip the four recursions of the accepted site run in
+// parallel, one per warp (warp 0: As, warp 1: Bs, warp 2: alpha, warp 3:
+// beta), each a length-m FP64 dot product per site; warp 0 keeps the current
+// diagonal G~_uu in registers and takes the decisions.
+// Shared: g (kb x (kb+1)), As/Bs/al/be (K x kb each, row m = accepted flip m).
+__global__ void __launch_bounds__(128)
+    metropolis_block_kernel(MetroArgs a, const void *__restrict__ g_, int g_is_f32, int8_t *s,
+                            const uint8_t *__restrict__ forced, double *__restrict__ alpha_out,
+                            double *__restrict__ beta_out, int *accept_count, int *status,
+                            unsigned long long *total) {
   extern __shared__ __align__(16) double sm[];
-  const int kb = a.kb, u = threadIdx.x;
+  const int kb = a.kb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ldg = kb + 1;
-  double *gs = sm;                    // kb * ldg
-  double *As = gs + kb * ldg;         // kb * kb  [m][u]
-  double *Bs = As + kb * kb;          // [m][u]
-  double *al = Bs + kb * kb;          // [m][u]
-  double *be = al + kb * kb;          // [m][u]
+  double *gs = sm;              // kb * ldg
+  double *As = gs + kb * ldg;   // [m][u]
+  double *Bs = As + kb * kb;
+  double *al = Bs + kb * kb;
+  double *be = al + kb * kb;
   // decision and coefficient of site j, double-buffered by the parity of j:
   // a rejected site has no second barrier, so the slot written at j + 2 must
   // differ from the one still being read at j
   __shared__ int s_dec[2];
   __shared__ double s_coef[2];
 
-  for (int e = u; e < kb * kb; e += blockDim.x) {
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
     const int r = e / kb, c = e % kb;
-    gs[r * ldg + c] = (double)g[(size_t)r * a.ld_g + c];
+    const size_t off = (size_t)r * a.ld_g + c;
+    gs[r * ldg + c] = g_is_f32 ? (double)static_cast<const float *>(g_)[off]
+                               : static_cast<const double *>(g_)[off];
   }
-  double dtil = 0.0, urand = 0.0;
-  int si = 1;
-  if (u < kb) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)(a.s0 + u), (uint32_t)a.slice0, a.c2, a.c3),
-                                  a.k0, a.k1);
-    urand = uniform53(r.x, r.y);
-    si = (int)s[a.s0 + u];
+  // warp 0: per-site state (sites lane and lane + 32)
+  double dtil[2] = {0.0, 0.0}, urand[2] = {0.0, 0.0};
+  int si[2] = {1, 1};
+  if (warp == 0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int u = lane + 32 * h;
+      if (u < kb) {
+        const uint4 r = philox4x32_10(
+            make_uint4((uint32_t)(a.s0 + u), (uint32_t)a.slice0, a.c2, a.c3), a.k0, a.k1);
+        urand[h] = uniform53(r.x, r.y);
+        si[h] = (int)s[a.s0 + u];
+      }
+    }
   }
   __syncthreads();
-  if (u < kb) dtil = gs[u * ldg + u];
+  if (warp == 0) {
+    if (lane < kb) dtil[0] = gs[lane * ldg + lane];
+    if (lane + 32 < kb) dtil[1] = gs[(lane + 32) * ldg + lane + 32];
+  }
 
   const double e2l = a.e2l, em2l = a.em2l;
   int m = 0;
   for (int j = 0; j < kb; ++j) {
-    if (u == j) {
+    if (warp == 0 && lane == (j & 31)) {
+      const int h = j >> 5;
       // delta = e^{-2 lambda s} - 1, r = 1 + delta (1 - G~_jj), R = e^{2 lambda s} r^2
-      const double delta = (si > 0 ? em2l : e2l) - 1.0;
-      const double r = 1.0 + delta * (1.0 - dtil);
-      const double R = (si > 0 ? e2l : em2l) * r * r;
+      const double delta = (si[h] > 0 ? em2l : e2l) - 1.0;
+      const double r = 1.0 + delta * (1.0 - dtil[h]);
+      const double R = (si[h] > 0 ? e2l : em2l) * r * r;
       int dec;
       if (!(R > 0.0) || !isfinite(R)) {
         dec = -1;
       } else if (forced) {
         dec = forced[j] ? 1 : 0;
       } else {
-        dec = (urand < R) ? 1 : 0;
+        dec = (urand[h] < R) ? 1 : 0;
       }
       s_dec[j & 1] = dec;
       s_coef[j & 1] = delta / r;
@@ -114,84 +174,112 @@ __global__ void metropolis_block_kernel(MetroArgs a, const TG *__restrict__ g, i
     __syncthreads();
     const int dec = s_dec[j & 1];
     if (dec < 0) {
-      if (u == 0) *status = 1;
+      if (threadIdx.x == 0) *status = 1;
       break;
     }
-    if (dec) {
-      const double c = s_coef[j & 1];
-      if (u < kb) {
-        double col = gs[u * ldg + j], row = gs[j * ldg + u];
-        double alv = (u == j) ? 1.0 : 0.0, bev = alv;
-        for (int mm = 0; mm < m; ++mm) {
-          const double bj = Bs[mm * kb + j], aj = As[mm * kb + j];
-          col -= As[mm * kb + u] * bj;
-          row -= aj * Bs[mm * kb + u];
-          alv -= al[mm * kb + u] * bj;
-          bev += aj * be[mm * kb + u];
-        }
-        const double acol = c * col;
-        const double brow = ((u == j) ? 1.0 : 0.0) - row;
-        As[m * kb + u] = acol;
-        Bs[m * kb + u] = brow;
-        al[m * kb + u] = c * alv;
-        be[m * kb + u] = bev;
-        dtil -= acol * brow;
+    if (!dec) continue;
+    const double c = s_coef[j & 1];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int u = lane + 32 * h;
+      if (u >= kb) continue;
+      const double dj = (u == j) ? 1.0 : 0.0;
+      if (warp == 0) {         // As_m[u] = c (g[u][j] - sum As_m'[u] Bs_m'[j])
+        double v = gs[u * ldg + j];
+        for (int mm = 0; mm < m; ++mm) v = fma(-As[mm * kb + u], Bs[mm * kb + j], v);
+        As[m * kb + u] = c * v;
+      } else if (warp == 1) {  // Bs_m[u] = delta_uj - (g[j][u] - sum As_m'[j] Bs_m'[u])
+        double v = gs[j * ldg + u];
+        for (int mm = 0; mm < m; ++mm) v = fma(-As[mm * kb + j], Bs[mm * kb + u], v);
+        Bs[m * kb + u] = dj - v;
+      } else if (warp == 2) {  // al_m[u] = c (delta_uj - sum al_m'[u] Bs_m'[j])
+        double v = dj;
+        for (int mm = 0; mm < m; ++mm) v = fma(-al[mm * kb + u], Bs[mm * kb + j], v);
+        al[m * kb + u] = c * v;
+      } else {                 // be_m[u] = delta_uj + sum As_m'[j] be_m'[u]
+        double v = dj;
+        for (int mm = 0; mm < m; ++mm) v = fma(As[mm * kb + j], be[mm * kb + u], v);
+        be[m * kb + u] = v;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int u = lane + 32 * h;
+        if (u < kb) dtil[h] -= As[m * kb + u] * Bs[m * kb + u];
         if (u == j) {
-          si = -si;
-          s[a.s0 + u] = (int8_t)si;
+          si[h] = -si[h];
+          s[a.s0 + u] = (int8_t)si[h];
         }
       }
-      ++m;
-      __syncthreads();
     }
+    ++m;
   }
-  // Gamma[u][w] = sum_m al[m][u] be[m][w]; full K x K, zero outside kb
-  for (int e = u; e < a.K * a.K; e += blockDim.x) {
-    const int r = e / a.K, c = e % a.K;
-    double acc = 0.0;
-    if (r < kb && c < kb)
-      for (int mm = 0; mm < m; ++mm) acc += al[mm * kb + r] * be[mm * kb + c];
-    Gamma[e] = acc;
+  // outputs: rows m' < m of alpha and beta (row stride K); the rest zero
+  for (int e = threadIdx.x; e < a.K * a.K; e += blockDim.x) {
+    const int r = e / a.K, u = e % a.K;
+    const bool ok = (r < m && u < kb);
+    alpha_out[e] = ok ? al[r * kb + u] : 0.0;
+    beta_out[e] = ok ? be[r * kb + u] : 0.0;
   }
-  if (u == 0) {
+  if (threadIdx.x == 0) {
     *accept_count = m;
     if (total) atomicAdd(total, (unsigned long long)m);
   }
 }
 
-template <typename TG>
-cudaError_t launch_metropolis(const MetroArgs &a, const TG *g, int8_t *s, const uint8_t *forced,
-                              double *Gamma, int *accept_count, int *status,
-                              unsigned long long *total, cudaStream_t st) {
+cudaError_t launch_metropolis(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
+                              const uint8_t *forced, double *alpha, double *beta, int *accept_count,
+                              int *status, unsigned long long *total, cudaStream_t st) {
   if (a.kb < 1 || a.kb > 64 || a.kb > a.K) return cudaErrorInvalidValue;
-  const int threads = a.kb <= 32 ? 32 : 64;
   const size_t smem = (size_t)(a.kb * (a.kb + 1) + 4 * a.kb * a.kb) * sizeof(double);
-  cudaError_t e = ensure_smem_attr((const void *)metropolis_block_kernel<TG>,
+  cudaError_t e = ensure_smem_attr((const void *)metropolis_block_kernel,
                                    (int)(5 * 64 * 65 * sizeof(double)));
   if (e != cudaSuccess) return e;
   DQ_KSCOPE(KF_METRO, st);
-  metropolis_block_kernel<TG><<<1, threads, smem, st>>>(a, g, s, forced, Gamma, accept_count,
-                                                         status, total);
+  metropolis_block_kernel<<<1, 128, smem, st>>>(a, g, g_f32 ? 1 : 0, s, forced, alpha, beta,
+                                                accept_count, status, total);
   return cudaGetLastError();
 }
-template cudaError_t launch_metropolis<double>(const MetroArgs &, const double *, int8_t *,
-                                               const uint8_t *, double *, int *, int *,
-                                               unsigned long long *, cudaStream_t);
-template cudaError_t launch_metropolis<float>(const MetroArgs &, const float *, int8_t *,
-                                              const uint8_t *, double *, int *, int *,
-                                              unsigned long long *, cudaStream_t);
 
-// ----------------------------------------------------------------- rank-k flush
-// G[:, J] -= Gcol W_J, W_J = Gamma (E_S - Grow)[:, J], one CTA per stripe J
-// of SW consecutive columns covering all N rows, so W_J (K x SW) is formed
+// ----------------------------------------------------------------- A = G[:,S] alpha
+// A[i][mm] = sum_{u < kb} Gcol[i][u] alpha[mm][u] for mm < m, zero for m <= mm < K.
+// FP64 arithmetic; output T (double / float) or, for the double-float flush,
+// a (hi, lo) FP32 pair.
+template <typename T, typename TA>
+__global__ void __launch_bounds__(256)
+    amat_kernel(int N, int K, int kb, int ldc, const T *__restrict__ Gcol,
+                const double *__restrict__ alpha, int lda, const int *__restrict__ accept_count,
+                TA *__restrict__ A) {
+  const int m = accept_count ? *accept_count : kb;
+  const int rows_per = 256 / K;
+  const int i = blockIdx.x * rows_per + threadIdx.x / K;
+  const int mm = threadIdx.x % K;
+  if (i >= N) return;
+  double v = 0.0;
+  if (mm < m) {
+    const T *gc = Gcol + (size_t)i * ldc;
+    const double *ar = alpha + (size_t)mm * lda;
+    for (int u = 0; u < kb; ++u) v = fma((double)gc[u], ar[u], v);
+  }
+  if constexpr (std::is_same<TA, float2>::value)
+    A[(size_t)i * K + mm] = split_df_bits(v);
+  else
+    A[(size_t)i * K + mm] = (TA)v;
+}
+
+// ----------------------------------------------------------------- rank-m flush
+// G[:, J] -= A B_J, B_J = [beta_m] (E_S - Grow)[:, J], one CTA per stripe J
+// of SW consecutive columns covering all N rows, so B_J (K x SW) is formed
 // once. Thread (rsub, col) owns column j0 + col and rows rsub, rsub + 256/SW,
-// ...; it keeps its column of W in registers and streams G once (read,
+// ...; it keeps its column of B in registers and streams G once (read,
 // subtract, write). The epilogue gathers the next block's rows / columns.
 //   T  = storage type of G (double or float)
-//   DF = FP64-accurate product on the FP32 units: Gcol holds (hi, lo) FP32
-//        pairs, W is split in registers, each MAC is an exact FP32 product
-//        plus cross terms accumulated with TwoSum (T must be double).
-__device__ __forceinline__ void df_mac2(float ah, float al, float bh, float bl, float &sh, float &sl) {
+//   DF = FP64-accurate product on the FP32 units: A and B as (hi, lo) FP32
+//        pairs, each MAC an exact FP32 product plus cross terms, accumulated
+//        with TwoSum (12 FP32 operations); T must be double.
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float &sh, float &sl) {
   const float p = ah * bh;
   float e = fmaf(ah, bh, -p);
   e = fmaf(ah, bl, e);
@@ -205,201 +293,160 @@ __device__ __forceinline__ void df_mac2(float ah, float al, float bh, float bl, 
 
 template <typename T, int K, int SW, bool DF>
 __global__ void __launch_bounds__(256)
-    flush_kernel(FlushArgs a, T *__restrict__ G, const void *__restrict__ Gcol_,
-                 const T *__restrict__ Grow, const double *__restrict__ Gamma,
-                 const int *__restrict__ accept_count, void *__restrict__ Gcol_next_,
+    flush_kernel(FlushArgs a, T *__restrict__ G, const void *__restrict__ A_,
+                 const T *__restrict__ Grow, const double *__restrict__ beta,
+                 const int *__restrict__ accept_count, T *__restrict__ Gcol_next,
                  T *__restrict__ Grow_next) {
   constexpr int RSTEP = 256 / SW;
-  __shared__ double Wsh[K][SW];
+  __shared__ double Bsh[K][SW];
   const int tid = threadIdx.x, col = tid % SW, rsub = tid / SW;
   const int N = a.N;
   const int j0 = blockIdx.x * SW, j = j0 + col;
   const bool jok = j < N;
-  const int m_acc = accept_count ? *accept_count : 1;
+  const int m = accept_count ? *accept_count : a.kb;
 
-  if (m_acc > 0) {
+  // B_J[mm][c] = beta[mm][j - s0] (j in S) - sum_u beta[mm][u] Grow[u][j]
+  if (m > 0) {
     for (int e = tid; e < K * SW; e += 256) {
-      const int p = e / SW, c = e % SW, jj = j0 + c;
+      const int mm = e / SW, c = e % SW, jj = j0 + c;
       double w = 0.0;
-      if (jj < N && p < a.kb) {
+      if (jj < N && mm < m) {
         const int js = jj - a.s0;
-        if (js >= 0 && js < a.kb) w = Gamma[p * K + js];
-        for (int q = 0; q < a.kb; ++q) w -= Gamma[p * K + q] * (double)Grow[(size_t)q * N + jj];
+        if (js >= 0 && js < a.kb) w = beta[mm * a.ldb + js];
+        for (int u = 0; u < a.kb; ++u) w = fma(-beta[mm * a.ldb + u], (double)Grow[(size_t)u * N + jj], w);
       }
-      Wsh[p][c] = w;
+      Bsh[mm][c] = w;
     }
   }
   __syncthreads();
 
   using WT = typename std::conditional<DF, float, T>::type;
-  WT wh[K], wl[DF ? K : 1];
+  WT bh[K], bl[DF ? K : 1];
 #pragma unroll
   for (int p = 0; p < K; ++p) {
-    const double w = (m_acc > 0) ? Wsh[p][col] : 0.0;
+    const double w = (m > 0) ? Bsh[p][col] : 0.0;
     if constexpr (DF) {
-      wh[p] = (float)w;
-      wl[p] = (float)(w - (double)wh[p]);
+      const float2 sp = split_df_bits(w);
+      bh[p] = sp.x;
+      bl[p] = sp.y;
     } else {
-      wh[p] = (T)w;
+      bh[p] = (T)w;
     }
   }
   if (!jok) return;
 
   for (int i = rsub; i < N; i += RSTEP) {
     T acc = T(0);
-    if (m_acc > 0) {
+    if (m > 0) {
       if constexpr (DF) {
-        const float2 *gc = static_cast<const float2 *>(Gcol_) + (size_t)i * a.ldc;
+        const float4 *ap = reinterpret_cast<const float4 *>(static_cast<const float2 *>(A_) + (size_t)i * K);
         float sh = 0.f, sl = 0.f;
-        if ((a.ldc & 1) == 0) {
 #pragma unroll
-          for (int p = 0; p < K; p += 2) {
-            if (p < a.kb) {
-              const float4 g = *reinterpret_cast<const float4 *>(gc + p);
-              df_mac2(g.x, g.y, wh[p], wl[p], sh, sl);
-              df_mac2(g.z, g.w, wh[p + 1], wl[p + 1], sh, sl);
-            }
+        for (int p = 0; p < K; p += 2) {
+          if (p < m) {
+            const float4 v = ap[p >> 1];
+            df_mac(v.x, v.y, bh[p], bl[p], sh, sl);
+            df_mac(v.z, v.w, bh[p + 1], bl[p + 1], sh, sl);
           }
-        } else {
-#pragma unroll
-          for (int p = 0; p < K; ++p)
-            if (p < a.kb) df_mac2(gc[p].x, gc[p].y, wh[p], wl[p], sh, sl);
         }
-        acc = (double)sh + (double)sl;
+        acc = f2d_bits(sh) + f2d_bits(sl);
       } else {
-        const T *gc = static_cast<const T *>(Gcol_) + (size_t)i * a.ldc;
-        if ((a.ldc & 3) == 0) {
-          // 16-byte vector loads; a group straddling kb stays inside the row
-          // (ldc >= kb rounded up to 4) and meets zero rows of W
+        const T *ap = static_cast<const T *>(A_) + (size_t)i * K;
 #pragma unroll
-          for (int p = 0; p < K; p += 4) {
-            if (p < a.kb) {
-              if constexpr (sizeof(T) == 4) {
-                const float4 g4 = *reinterpret_cast<const float4 *>(gc + p);
-                acc = fmaf(g4.x, wh[p], acc);
-                acc = fmaf(g4.y, wh[p + 1], acc);
-                acc = fmaf(g4.z, wh[p + 2], acc);
-                acc = fmaf(g4.w, wh[p + 3], acc);
-              } else {
-                const double2 g0 = *reinterpret_cast<const double2 *>(gc + p);
-                const double2 g1 = *reinterpret_cast<const double2 *>(gc + p + 2);
-                acc = fma(g0.x, wh[p], acc);
-                acc = fma(g0.y, wh[p + 1], acc);
-                acc = fma(g1.x, wh[p + 2], acc);
-                acc = fma(g1.y, wh[p + 3], acc);
-              }
+        for (int p = 0; p < K; p += 4) {
+          if (p < m) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 g4 = *reinterpret_cast<const float4 *>(ap + p);
+              acc = fmaf(g4.x, bh[p], acc);
+              acc = fmaf(g4.y, bh[p + 1], acc);
+              acc = fmaf(g4.z, bh[p + 2], acc);
+              acc = fmaf(g4.w, bh[p + 3], acc);
+            } else {
+              const double2 g0 = *reinterpret_cast<const double2 *>(ap + p);
+              const double2 g1 = *reinterpret_cast<const double2 *>(ap + p + 2);
+              acc = fma(g0.x, bh[p], acc);
+              acc = fma(g0.y, bh[p + 1], acc);
+              acc = fma(g1.x, bh[p + 2], acc);
+              acc = fma(g1.y, bh[p + 3], acc);
             }
           }
-        } else {
-#pragma unroll
-          for (int p = 0; p < K; ++p)
-            if (p < a.kb) acc = fma(gc[p], wh[p], acc);
         }
       }
     }
     T *gp = G + (size_t)i * N + j;
     const T val = *gp - acc;
-    if (m_acc > 0) *gp = val;
+    if (m > 0) *gp = val;
     if (a.nkb > 0) {
       const int it = i - a.ns0, jt = j - a.ns0;
       if (it >= 0 && it < a.nkb) Grow_next[(size_t)it * N + j] = val;
-      if (jt >= 0 && jt < K) {
-        if constexpr (DF) {
-          float2 *gn = static_cast<float2 *>(Gcol_next_) + (size_t)i * K + jt;
-          if (jt < a.nkb) {
-            const float h = (float)val;
-            *gn = make_float2(h, (float)(val - (double)h));
-          } else {
-            *gn = make_float2(0.f, 0.f);
-          }
-        } else {
-          static_cast<T *>(Gcol_next_)[(size_t)i * K + jt] = (jt < a.nkb) ? val : T(0);
-        }
-      }
+      if (jt >= 0 && jt < K) Gcol_next[(size_t)i * K + jt] = (jt < a.nkb) ? val : T(0);
     }
   }
 }
 
 template <typename T, int K, bool DF>
-static cudaError_t launch_flush_K(const FlushArgs &a, T *G, const void *Gcol, const T *Grow,
-                                  const double *Gamma, const int *acc, void *Gcol_next,
-                                  T *Grow_next, cudaStream_t st) {
+static cudaError_t launch_flush_K(const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
+                                  const double *alpha, const double *beta, const int *acc,
+                                  void *Abuf, T *Gcol_next, T *Grow_next, cudaStream_t st) {
+  {
+    const int rows_per = 256 / K;
+    DQ_KSCOPE(KF_OTHER, st);
+    add_work(KF_OTHER, 2.0 * a.N * (double)a.kb * a.kb, 8.0 * a.N * (double)(a.kb + K));
+    if constexpr (DF)
+      amat_kernel<T, float2><<<(a.N + rows_per - 1) / rows_per, 256, 0, st>>>(
+          a.N, K, a.kb, a.ldc, Gcol, alpha, a.lda, acc, static_cast<float2 *>(Abuf));
+    else
+      amat_kernel<T, T><<<(a.N + rows_per - 1) / rows_per, 256, 0, st>>>(
+          a.N, K, a.kb, a.ldc, Gcol, alpha, a.lda, acc, static_cast<T *>(Abuf));
+  }
   constexpr int SW = 4;
   const int grid = (a.N + SW - 1) / SW;
   DQ_KSCOPE(KF_FLUSH, st);
-  // rank-kb update of the N x N G: 2 N^2 kb flops (+ 2 kb^2 N for W); G read
-  // and written once, Gcol and Grow read once
-  add_work(KF_FLUSH, 2.0 * a.N * (double)a.N * a.kb + 2.0 * a.kb * (double)a.kb * a.N,
-           (2.0 * a.N * (double)a.N + 2.0 * a.N * (double)a.kb) * sizeof(T));
-  flush_kernel<T, K, SW, DF><<<grid, 256, 0, st>>>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next);
+  // rank-m update of the N x N G, m = accepted flips (<= kb): 2 N^2 m flops,
+  // counted at m = kb (an upper bound; the kernel skips the unused terms);
+  // G read and written once, A read once
+  add_work(KF_FLUSH, 2.0 * a.N * (double)a.N * a.kb,
+           (2.0 * a.N * (double)a.N + (double)a.N * a.kb) * sizeof(T));
+  flush_kernel<T, K, SW, DF><<<grid, 256, 0, st>>>(a, G, Abuf, Grow, beta, acc, Gcol_next, Grow_next);
   return cudaGetLastError();
 }
 
 template <typename T, bool DF>
-static cudaError_t launch_flush_any(int K, const FlushArgs &a, T *G, const void *Gcol, const T *Grow,
-                                    const double *Gamma, const int *acc, void *Gcol_next, T *Grow_next,
-                                    cudaStream_t st) {
+static cudaError_t launch_flush_any(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
+                                    const double *alpha, const double *beta, const int *acc,
+                                    void *Abuf, T *Gcol_next, T *Grow_next, cudaStream_t st) {
   switch (K) {
-    case 4: return launch_flush_K<T, 4, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    case 8: return launch_flush_K<T, 8, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    case 16: return launch_flush_K<T, 16, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    case 32: return launch_flush_K<T, 32, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-    case 64: return launch_flush_K<T, 64, DF>(a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
+#define DQ_FLUSH_CASE(KK) \
+  case KK: return launch_flush_K<T, KK, DF>(a, G, Gcol, Grow, alpha, beta, acc, Abuf, Gcol_next, Grow_next, st);
+    DQ_FLUSH_CASE(4)
+    DQ_FLUSH_CASE(8)
+    DQ_FLUSH_CASE(16)
+    DQ_FLUSH_CASE(32)
+    DQ_FLUSH_CASE(64)
+#undef DQ_FLUSH_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
 cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
-                         const double *Gamma, const int *acc, T *Gcol_next, T *Grow_next,
-                         cudaStream_t st) {
-  return launch_flush_any<T, false>(K, a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
+                         const double *alpha, const double *beta, const int *acc, void *Abuf,
+                         T *Gcol_next, T *Grow_next, bool df, cudaStream_t st) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (df)
+      return launch_flush_any<double, true>(K, a, G, Gcol, Grow, alpha, beta, acc, Abuf, Gcol_next,
+                                            Grow_next, st);
+  }
+  return launch_flush_any<T, false>(K, a, G, Gcol, Grow, alpha, beta, acc, Abuf, Gcol_next,
+                                    Grow_next, st);
 }
 template cudaError_t launch_flush<double>(int, const FlushArgs &, double *, const double *,
-                                          const double *, const double *, const int *, double *,
-                                          double *, cudaStream_t);
+                                          const double *, const double *, const double *,
+                                          const int *, void *, double *, double *, bool,
+                                          cudaStream_t);
 template cudaError_t launch_flush<float>(int, const FlushArgs &, float *, const float *,
-                                         const float *, const double *, const int *, float *,
-                                         float *, cudaStream_t);
-
-cudaError_t launch_flush_df(int K, const FlushArgs &a, double *G, const float2 *Gcol,
-                            const double *Grow, const double *Gamma, const int *acc,
-                            float2 *Gcol_next, double *Grow_next, cudaStream_t st) {
-  return launch_flush_any<double, true>(K, a, G, Gcol, Grow, Gamma, acc, Gcol_next, Grow_next, st);
-}
-
-// Gather for the double-float flush: Gcol as (hi, lo) FP32 pairs, Grow in FP64.
-__global__ void gather_block_df_kernel(int N, int s0, int kb, int K, const double *__restrict__ G,
-                                       float2 *__restrict__ Gcol, double *__restrict__ Grow) {
-  const long total = (long)N * K;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / K), t = (int)(e % K);
-    float2 v = make_float2(0.f, 0.f);
-    if (t < kb) {
-      const double x = G[(size_t)i * N + s0 + t];
-      const float h = (float)x;
-      v = make_float2(h, (float)(x - (double)h));
-    }
-    Gcol[e] = v;
-  }
-  const long total2 = (long)kb * N;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total2;
-       e += (long)gridDim.x * blockDim.x) {
-    const int t = (int)(e / N), j = (int)(e % N);
-    Grow[e] = G[(size_t)(s0 + t) * N + j];
-  }
-}
-
-cudaError_t launch_gather_df(int N, int s0, int kb, int K, const double *G, float2 *Gcol,
-                             double *Grow, cudaStream_t st) {
-  const long work = (long)N * K;
-  int grid = (int)((work + 255) / 256);
-  if (grid > 4096) grid = 4096;
-  if (grid < 1) grid = 1;
-  DQ_KSCOPE(KF_OTHER, st);
-  gather_block_df_kernel<<<grid, 256, 0, st>>>(N, s0, kb, K, G, Gcol, Grow);
-  return cudaGetLastError();
-}
+                                         const float *, const double *, const double *,
+                                         const int *, void *, float *, float *, bool,
+                                         cudaStream_t);
 
 }  // namespace dq

@@ -46,34 +46,42 @@ def propagate(L, scale, side, X, Y=None, pre=None, post=None, vscale=None):
 
 
 def metropolis_block(N, site0, kb, g, s, lam, seed, chain, sweep_pass, slice1, forced=None):
-    """One delayed-update block (FP64): returns (Gamma, accepted, status)."""
+    """One delayed-update block (FP64): returns (alpha, beta, count, status) with
+    count a device int32 tensor (pass it to flush) -- alpha/beta rows < count
+    hold the coefficient vectors of the accepted flips."""
     import torch
     lib = _lib.load()
     _need(g, torch.float64, "g")
     _need(s, torch.int8, "s")
     dev = g.device
-    Gamma = torch.empty((kb, kb), dtype=torch.float64, device=dev)
+    alpha = torch.empty((kb, kb), dtype=torch.float64, device=dev)
+    beta = torch.empty((kb, kb), dtype=torch.float64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     if forced is not None:
         forced = forced.to(device=dev, dtype=torch.uint8).contiguous()
     check(lib.dqmc_op_metropolis_block(int(N), int(site0), int(kb), _ptr(g), int(g.shape[1]), _ptr(s),
                                        float(lam), int(seed), int(chain), int(sweep_pass), int(slice1),
-                                       _ptr(forced), _ptr(Gamma), _ptr(cnt), _ptr(st), _stream(torch)))
-    return Gamma, int(cnt.item()), int(st.item())
+                                       _ptr(forced), _ptr(alpha), _ptr(beta), _ptr(cnt), _ptr(st),
+                                       _stream(torch)))
+    return alpha, beta, cnt, int(st.item())
 
 
-def flush(N, site0, kb, G, Gcol, Grow, Gamma):
-    """G <- G - Gcol Gamma (E_S - Grow) in place (FP64 or FP32 G)."""
+def flush(N, site0, kb, G, Gcol, Grow, alpha, beta, count, mode=None):
+    """G <- G - (Gcol alpha^T)(beta (E_S - Grow)) in place. mode: "f64" (default for
+    float64 G), "df" (FP64 G, double-float product) or "f32" (float32 G)."""
     import torch
     lib = _lib.load()
     dt = G.dtype
-    _need(G, dt, "G")
-    _need(Gcol, dt, "Gcol")
-    _need(Grow, dt, "Grow")
-    _need(Gamma, torch.float64, "Gamma")
-    fn = lib.dqmc_op_flush_f64 if dt == torch.float64 else lib.dqmc_op_flush_f32
-    check(fn(int(N), int(site0), int(kb), _ptr(G), _ptr(Gcol), _ptr(Grow), _ptr(Gamma), _stream(torch)))
+    for t, n in ((G, "G"), (Gcol, "Gcol"), (Grow, "Grow")):
+        _need(t, dt, n)
+    _need(alpha, torch.float64, "alpha")
+    _need(beta, torch.float64, "beta")
+    _need(count, torch.int32, "count")
+    mode = mode or ("f64" if dt == torch.float64 else "f32")
+    fn = {"f64": lib.dqmc_op_flush_f64, "df": lib.dqmc_op_flush_df, "f32": lib.dqmc_op_flush_f32}[mode]
+    check(fn(int(N), int(site0), int(kb), _ptr(G), _ptr(Gcol), _ptr(Grow), _ptr(alpha), _ptr(beta),
+             _ptr(count), _stream(torch)))
     return G
 
 
@@ -87,3 +95,23 @@ def measure(L, G, site_offsets=True):
     check(lib.dqmc_op_measure(int(L), _ptr(G), int(bool(site_offsets)), out.ctypes.data_as(C.c_void_p),
                               _stream(torch)))
     return dict(zip(("S_pair_G", "S_pair_dk", "phi2_G", "phi2_K", "density", "ekin"), out.tolist()))
+
+
+def gemm(A, B, C=None, alpha=1.0, beta=0.0, ta=False, tb=False, mode="f64"):
+    """C = alpha op(A) op(B) + beta C (FP64 tensors). mode: "f64" (FP64 FMA),
+    "df" (double-float on the FP32 units), "oz" (exact digit slices on the bf16
+    tensor cores)."""
+    import torch
+    lib = _lib.load()
+    for t, n in ((A, "A"), (B, "B")):
+        _need(t, torch.float64, n)
+    M = A.shape[1] if ta else A.shape[0]
+    K = A.shape[0] if ta else A.shape[1]
+    N = B.shape[0] if tb else B.shape[1]
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
+    _need(C, torch.float64, "C")
+    check(lib.dqmc_op_gemm_f64({"f64": 0, "df": 1, "oz": 2}[mode], int(ta), int(tb), M, N, K, float(alpha),
+                               _ptr(A), A.shape[1], _ptr(B), B.shape[1], float(beta), _ptr(C), C.shape[1],
+                               _stream(torch)))
+    return C

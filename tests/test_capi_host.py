@@ -92,6 +92,11 @@ def test_operator_argument_validation(lib):
     assert lib.dqmc_op_propagate_f64(5, -0.1, 0, C.c_void_p(16), C.c_void_p(16), 1, 1, None, None, None, None) == 1
     assert lib.dqmc_op_propagate_f64(4, -0.1, 2, C.c_void_p(16), C.c_void_p(16), 1, 1, None, None, None, None) == 1
     assert lib.dqmc_op_propagate_f64(4, -0.1, 1, C.c_void_p(16), C.c_void_p(16), 1, 10, None, None, None, None) == 1
-    assert lib.dqmc_op_flush_f64(48, 40, 16, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), None) == 1
-    assert lib.dqmc_op_metropolis_block(48, 0, 65, C.c_void_p(16), 65, C.c_void_p(16), 0.5, 1, 0, 0, 1,
-                                        None, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), None) == 1
+    p = C.c_void_p(16)
+    assert lib.dqmc_op_flush_f64(48, 40, 16, p, p, p, p, p, p, None) == 1      # site0 + kb > N
+    assert lib.dqmc_op_flush_df(48, 0, 65, p, p, p, p, p, p, None) == 1        # kb > 64
+    assert lib.dqmc_op_flush_f32(48, 0, 8, p, p, p, None, p, p, None) == 1     # null alpha
+    assert lib.dqmc_op_metropolis_block(48, 0, 65, p, 65, p, 0.5, 1, 0, 0, 1,
+                                        None, p, p, p, p, None) == 1
+    assert lib.dqmc_op_metropolis_block(48, 0, 8, p, 4, p, 0.5, 1, 0, 0, 1,
+                                        None, p, p, p, p, None) == 1           # ld_g < kb

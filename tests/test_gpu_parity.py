@@ -94,8 +94,10 @@ def _oracle_slice_update(L, beta, U, G0, field, l, pas, seed, sweep):
     return ch.G, ch.field
 
 
-@pytest.mark.parametrize("L,k", [(2, 4), (4, 8), (4, 32), (6, 64), (6, 16)])
-def test_delayed_update_slice_matches_one_at_a_time(pkg, L, k):
+@pytest.mark.parametrize("L,k,mode", [(2, 4, "f64"), (4, 8, "f64"), (4, 32, "f64"), (6, 64, "f64"),
+                                      (6, 16, "f64"), (6, 7, "f64"), (4, 32, "df"), (6, 64, "df"),
+                                      (6, 12, "df")])
+def test_delayed_update_slice_matches_one_at_a_time(pkg, L, k, mode):
     """A whole slice of proposals by blocks of k (Metropolis block + rank-k
     flush) reproduces the oracle's one-at-a-time Sherman-Morrison sweep: same
     decisions from the same Philox stream, same G."""
@@ -113,11 +115,11 @@ def test_delayed_update_slice_matches_one_at_a_time(pkg, L, k):
         Gcol = G[:, s0:s0 + kb].contiguous()
         Grow = G[s0:s0 + kb, :].contiguous()
         g = G[s0:s0 + kb, s0:s0 + kb].contiguous()
-        Gam, nacc, st = pkg.ops.metropolis_block(N, s0, kb, g, s, m.lam, seed, 0, 2 * sweep + pas, l)
+        al, be, cnt, st = pkg.ops.metropolis_block(N, s0, kb, g, s, m.lam, seed, 0, 2 * sweep + pas, l)
         assert st == 0
-        pkg.ops.flush(N, s0, kb, G, Gcol, Grow, Gam)
+        pkg.ops.flush(N, s0, kb, G, Gcol, Grow, al, be, cnt, mode=mode)
     assert np.array_equal(s.cpu().numpy(), fref[l - 1])
-    assert np.max(np.abs(G.cpu().numpy() - Gref)) < 1e-12
+    assert np.max(np.abs(G.cpu().numpy() - Gref)) < (1e-12 if mode == "f64" else 1e-11)
 
 
 def test_forced_flips_and_fp32_flush(pkg):
@@ -137,12 +139,13 @@ def test_forced_flips_and_fp32_flush(pkg):
     s32 = s.clone()
     for s0 in range(0, N, k):
         f = dev(forced[s0:s0 + k], torch.uint8)
-        Gam, _, _ = pkg.ops.metropolis_block(N, s0, k, G[s0:s0 + k, s0:s0 + k].contiguous(), s, m.lam,
-                                             1, 0, 0, 1, forced=f)
-        pkg.ops.flush(N, s0, k, G, G[:, s0:s0 + k].contiguous(), G[s0:s0 + k, :].contiguous(), Gam)
+        al, be, cnt, _ = pkg.ops.metropolis_block(N, s0, k, G[s0:s0 + k, s0:s0 + k].contiguous(), s, m.lam,
+                                                  1, 0, 0, 1, forced=f)
+        pkg.ops.flush(N, s0, k, G, G[:, s0:s0 + k].contiguous(), G[s0:s0 + k, :].contiguous(), al, be, cnt)
         g32 = G32[s0:s0 + k, s0:s0 + k].double().contiguous()
-        Gam32, _, _ = pkg.ops.metropolis_block(N, s0, k, g32, s32, m.lam, 1, 0, 0, 1, forced=f)
-        pkg.ops.flush(N, s0, k, G32, G32[:, s0:s0 + k].contiguous(), G32[s0:s0 + k, :].contiguous(), Gam32)
+        al32, be32, cnt32, _ = pkg.ops.metropolis_block(N, s0, k, g32, s32, m.lam, 1, 0, 0, 1, forced=f)
+        pkg.ops.flush(N, s0, k, G32, G32[:, s0:s0 + k].contiguous(), G32[s0:s0 + k, :].contiguous(),
+                      al32, be32, cnt32)
     assert np.array_equal(s.cpu().numpy(), ch.field[0])
     assert np.max(np.abs(G.cpu().numpy() - ch.G)) < 1e-12
     assert np.max(np.abs(G32.double().cpu().numpy() - ch.G)) < 1e-5
@@ -281,3 +284,49 @@ def test_allocator_failure_reports_enomem(pkg):
     assert lib.dqmc_sweep(h, 1, 0) == 2  # DQMC_ENOMEM
     assert calls
     lib.dqmc_destroy(h)
+
+
+# ------------------------------------------------------------------ FP64-accurate GEMM variants
+@pytest.mark.parametrize("mode", ["f64", "df", "oz"])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+def test_gemm_variants_are_fp64_accurate(pkg, mode, ta, tb):
+    """FP64 FMA, double-float and tensor-core digit-slice GEMMs against numpy
+    FP64, normwise |C - C_ref| <= tol |op(A)||op(B)| + |C0|. Rows of op(A) and
+    columns of op(B) carry scales over 2^+-20 (the digit slices are exact
+    relative to the largest entry of each row of op(A) / column of op(B))."""
+    rng = np.random.default_rng(3)
+    M, N, K = 131, 77, 203                       # ragged against every tile
+    opA = rng.standard_normal((M, K)) * np.exp2(rng.integers(-20, 20, size=(M, 1)))
+    opB = rng.standard_normal((K, N)) * np.exp2(rng.integers(-20, 20, size=(1, N)))
+    A = np.ascontiguousarray(opA.T) if ta else opA
+    B = np.ascontiguousarray(opB.T) if tb else opB
+    C0 = rng.standard_normal((M, N))
+    ref = 0.7 * opA @ opB - 0.3 * C0
+    C = dev(C0)
+    pkg.ops.gemm(dev(A), dev(B), C, alpha=0.7, beta=-0.3, ta=ta, tb=tb, mode=mode)
+    bound = np.abs(opA) @ np.abs(opB) + np.abs(C0)
+    rel = np.max(np.abs(C.cpu().numpy() - ref) / bound)
+    tol = {"f64": 1e-14, "df": 1e-13, "oz": 1e-14}[mode]
+    assert rel < tol, rel
+    # agreement with the FP64 FMA GEMM at the FP64 rounding level
+    if mode != "f64":
+        C64 = dev(C0)
+        pkg.ops.gemm(dev(A), dev(B), C64, alpha=0.7, beta=-0.3, ta=ta, tb=tb, mode="f64")
+        err = np.max(np.abs(C.cpu().numpy() - C64.cpu().numpy()) / bound)
+        assert err < {"df": 1e-13, "oz": 2e-15}[mode], err
+
+
+def test_digit_slice_gemm_accuracy_is_relative_to_row_scale(pkg):
+    """With a dynamic range along K, digit slices lose the entries far below
+    the row maximum: the error is bounded by 2^-56 K max|row| max|col|, not by
+    |A||B|. (This is why the stabilisation uses them only on its orthogonal-
+    factor products.)"""
+    rng = np.random.default_rng(5)
+    M, N, K = 64, 64, 256
+    A = rng.standard_normal((M, K)) * np.exp2(rng.integers(-30, 0, size=(1, K)))
+    B = rng.standard_normal((K, N))
+    C = pkg.ops.gemm(dev(A), dev(B), mode="oz")
+    ref = A @ B
+    rowmax = np.abs(A).max(axis=1, keepdims=True)
+    colmax = np.abs(B).max(axis=0, keepdims=True)
+    assert np.max(np.abs(C.cpu().numpy() - ref) / (rowmax * colmax)) < K * 2.0 ** -55
