@@ -168,6 +168,49 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def prop_microbench(L, prec, nstack, reps=5):
+    """Left propagation e^{-dtau K} X (Eq. 5-6) on a stacked operand X of
+    nstack N x N blocks side by side (N x nstack N, larger than L2), in place;
+    returns the algorithmic HBM rate (one read + one write of X per launch)."""
+    import numpy as np
+    import torch
+
+    import paper_2608_03894_gb300 as pkg
+    N = 3 * L * L
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    X = torch.randn((N, nstack * N), dtype=dt, device="cuda")
+    df = prec == "df"
+    for _ in range(2):
+        pkg.ops.propagate(L, -0.1, 0, X, Y=X, df=df)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        pkg.ops.propagate(L, -0.1, 0, X, Y=X, df=df)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = 2.0 * X.numel() * X.element_size()
+    L2 = float(L * L)
+    flops = (15.0 * L2 * np.log2(L2) + 36.0 * L2) * nstack * N
+    del X
+    return {"L": L, "arith": prec, "operand_MB": round(nbytes / 2 / 1e6, 1), "ms_per_launch": round(ms, 4),
+            "GB_s": round(nbytes / (ms * 1e-3) / 1e9, 1), "TFLOP_s": round(flops / (ms * 1e-3) / 1e12, 3)}
+
+
+def run_micro(args):
+    import torch
+    torch.cuda.set_device(0)
+    peaks, src = load_peaks()
+    out = []
+    for prec in args.micro_prec.split(","):
+        r = prop_microbench(args.micro_L, prec, args.micro_stack)
+        r["frac_of_hbm"] = round(r["GB_s"] / peaks["hbm_gbs"], 3)
+        r["hbm_peak_source"] = src
+        out.append(r)
+    print(json.dumps({"micro": "prop", "results": out}), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import ctypes as C
 
@@ -278,6 +321,16 @@ def run_ours(args, rank, world, local_rank):
     roof["traffic"] = None
     roof["share_of_device_time"] = fd["ms"] / max(total_ms, 1e-9)
 
+    # FFT propagation alone on a stacked operand larger than L2 (HBM roofline of
+    # the propagation kernels, FP32 / double-float / FP64 arithmetic)
+    fft = None
+    if rank == 0:
+        fft = []
+        for prec in ("fp32", "df", "fp64"):
+            r = prop_microbench(L, prec, max(1, (800 << 20) // (N * N * 4)))
+            r["frac_of_hbm"] = round(r["GB_s"] / peaks["hbm_gbs"], 3)
+            fft.append(r)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle_sample(w, budget_s=args.cpu_budget)
@@ -287,14 +340,17 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "mixed": "f64-accurate (f32-pair) bulk + f64", "fp32": "f32 + f64 stab"}[w["precision"]],
+            "dtype": {"fp64": "f64", "mixed": "f64 (emulated on f32 pairs and bf16 digit slices) + f64",
+                      "fp32": "f32 + f64 stab"}[w["precision"]],
             "data": "synthetic (Philox-initialised Ising field, seed 1 + rank)",
             "config": config_dict(w, world),
             "max_drift": st["max_drift"],
             "acceptance": st["accepted"] / max(1, st["proposed"]),
             "sweeps_per_s": args.steps * world / (ms / 1000.0),
             "phase_breakdown_ms": {f: round(v["ms"], 3) for f, v in fam.items()},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "launches_before_timed": int(launches0),
+            "roofline": roof, "fft_roofline": fft, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches),
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -313,6 +369,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--micro", default=None, choices=("prop",),
+                    help="only the FFT propagation microbenchmark (stacked operand larger than L2)")
+    ap.add_argument("--micro-L", type=int, default=24)
+    ap.add_argument("--micro-stack", type=int, default=64)
+    ap.add_argument("--micro-prec", default="fp32,df,fp64")
     args = ap.parse_args()
     args_global = args
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -320,6 +381,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.micro:
+        if rank == 0:
+            run_micro(args)
         return
     if world > 1:
         import torch

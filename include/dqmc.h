@@ -103,18 +103,26 @@ typedef struct {
 dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, uint64_t seed,
                         dqmc_ctx **out);
 
-/* Options (numbers): "k" delay rank (1..64, default 32), "n_stab" slices between
- * UDV refreshes (default 10), "precision" (0 = plain FP64, 1 = FP32 propagation
- * and flush with FP64 stabilisation and ratios), "chain" (Philox chain id),
- * "timing" (1 = per-phase CUDA-event timers, 2 = also per kernel family; the
- * events themselves cost time, so time throughput with 0), "site_offsets" (1 = S_Pair phases
- * use site positions R + tau_a, 0 = cell positions), "bin" (measurements per
- * bin, default 10), "drift_limit" (hard limit, default 1e-3 -> DQMC_ENUMERIC),
- * "df_flush" / "df_stab" (mixed precision only, default 1: run the rank-m
- * flush / the stabilisation GEMMs as double-float products; 0 = native FP64).
- * "k", "n_stab", "precision", "chain", "df_flush" and "df_stab" are accepted
- * only before the first sweep; later they return DQMC_ESTATE. Precision 2
- * ("fp32") runs plain FP32 propagation and flush. */
+/* Options (numbers): "k" delay rank (4, 8, 16, 32 or 64; default 32), "n_stab"
+ * slices between UDV refreshes (default 10), "precision" (0 = plain FP64;
+ * 1 = mixed: FP64 data, ratios and recursions; propagation and flush in
+ * double-float arithmetic (FP32 pairs) on the FP32 units, stabilisation
+ * products as exact digit slices on the bf16 tensor cores; 2 = plain FP32
+ * propagation and flush, which
+ * drifts by 1e-3..1e-1 per refresh interval and exists for comparison),
+ * "chain" (Philox chain id), "timing" (1 = per-phase CUDA-event timers,
+ * 2 = also per kernel family; the events themselves cost time, so time
+ * throughput with 0), "site_offsets" (1 = S_Pair phases use site positions
+ * R + tau_a, 0 = cell positions), "bin" (measurements per bin, default 10),
+ * "drift_limit" (hard limit, default 1e-3 -> DQMC_ENUMERIC), and, for the mixed
+ * precision only: "df_flush" (default 1: the rank-m flush as double-float
+ * products; 0 = native FP64), "df_prop" (default 1: the FFT propagation in
+ * double-float arithmetic; 0 = native FP64), "stab_gemm" (stabilisation GEMMs: 0 = native
+ * FP64, 1 = double-float, 2 = exact 7-bit digit slices on the bf16 tensor
+ * cores, default 2), "gemm_sites" (32-bit mask of the stabilisation GEMM call
+ * sites that use the stab_gemm variant, default all).
+ * "k", "n_stab", "precision", "chain", "df_flush", "df_prop" and "stab_gemm" are accepted
+ * only before the first sweep; later they return DQMC_ESTATE. */
 dqmc_status dqmc_set_option(dqmc_ctx *ctx, const char *key, double value);
 
 /* Launch every kernel of this context on the given cudaStream_t (e.g. the
@@ -155,6 +163,21 @@ dqmc_status dqmc_get_stats(dqmc_ctx *ctx, dqmc_stats *out);
 dqmc_status dqmc_get_field(dqmc_ctx *ctx, int8_t *s_out);
 dqmc_status dqmc_set_field(dqmc_ctx *ctx, const int8_t *s);
 
+/* Replay (forced flips through the fast path), for measuring |dG| against an
+ * exact G. Starting from the fresh G at tau = 0 of the current field, runs the
+ * up pass l = 1..slice exactly as dqmc_sweep does (wrap, delayed-update blocks
+ * of rank k in the context's precision, UDV refreshes at the checkpoints
+ * before `slice`), except that every decision is forced: site i of slice l
+ * flips iff its spin differs from target[(l-1)*N + i]. G_out (N*N doubles,
+ * caller-owned host memory, row-major) receives the running G(tau_slice) of
+ * the fast path, before any refresh at that slice. Afterwards slices
+ * 1..slice of the field equal the target and the others are unchanged; the
+ * stacks are rebuilt by the next call. The flips count as accepted proposals
+ * in dqmc_stats. Sequential Sherman-Morrison / Woodbury update of Sec. II
+ * with the wrap of Eq. 5-6. DQMC_EINVAL on NULL pointers, a slice outside
+ * [1, M] or target values other than +-1. */
+dqmc_status dqmc_replay(dqmc_ctx *ctx, const int8_t *target, int slice, double *G_out);
+
 /* Checkpoint: parameters, options, field, sweep counter, statistics and bins.
  * G is recomputed on load. Binary file; DQMC_EINVAL if the file does not match
  * the context's (L, beta, dtau, U, mu). */
@@ -180,12 +203,16 @@ const char *dqmc_version(void);
  *     Y = diag(vscale) X diag(pre) e^{scale K} diag(post)
  * X, Y: N x nvec (side 0) or nvec x N (side 1) row-major with leading dimension
  * ld >= (side 0 ? nvec : N); Y may alias X. pre/post: length N or NULL;
- * vscale: length nvec or NULL. _f64: double data and vectors, _f32: float. The
- * 3x3 momentum blocks e^{scale H(k)} are built on the host in FP64 (cached per
- * (L, scale)). */
+ * vscale: length nvec or NULL. _f64: double data and vectors, _f32: float,
+ * _df: double data and vectors, computed in double-float arithmetic (pairs of
+ * FP32, ~2^-47 relative) on the FP32 units. The 3x3 momentum blocks
+ * e^{scale H(k)} are built on the host in FP64 (cached per (L, scale)). */
 dqmc_status dqmc_op_propagate_f64(int L, double scale, int side, const double *X, double *Y,
                                   int nvec, int ld, const double *pre, const double *post,
                                   const double *vscale, void *stream);
+dqmc_status dqmc_op_propagate_df(int L, double scale, int side, const double *X, double *Y,
+                                 int nvec, int ld, const double *pre, const double *post,
+                                 const double *vscale, void *stream);
 dqmc_status dqmc_op_propagate_f32(int L, double scale, int side, const float *X, float *Y,
                                   int nvec, int ld, const float *pre, const float *post,
                                   const float *vscale, void *stream);

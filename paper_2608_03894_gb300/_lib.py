@@ -54,11 +54,13 @@ SIGNATURES = {
     "dqmc_get_stats": (i32, [vp, C.POINTER(Stats)]),
     "dqmc_get_field": (i32, [vp, vp]),
     "dqmc_set_field": (i32, [vp, vp]),
+    "dqmc_replay": (i32, [vp, vp, i32, vp]),
     "dqmc_save": (i32, [vp, C.c_char_p]),
     "dqmc_load": (i32, [vp, C.c_char_p]),
     "dqmc_destroy": (None, [vp]),
     "dqmc_op_propagate_f64": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_propagate_f32": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
+    "dqmc_op_propagate_df": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_metropolis_block": (i32, [i32, i32, i32, vp, i32, vp, f64, u64, u32, u32, i32, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_f64": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_df": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),

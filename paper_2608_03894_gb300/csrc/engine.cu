@@ -130,12 +130,17 @@ static dqmc_status get_table(int L, double scale, int prec, const void **out) {
     for (size_t q = 0; q < tab.size(); ++q) h[q] = cpx<double>{tab[q].real(), tab[q].imag()};
     DQ_CUDA(cudaMalloc(&d, h.size() * sizeof(cpx<double>)));
     DQ_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(cpx<double>), cudaMemcpyHostToDevice));
-  } else {
+  } else if (prec == 1) {
     std::vector<cpx<float>> h(tab.size());
     for (size_t q = 0; q < tab.size(); ++q)
       h[q] = cpx<float>{(float)tab[q].real(), (float)tab[q].imag()};
     DQ_CUDA(cudaMalloc(&d, h.size() * sizeof(cpx<float>)));
     DQ_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(cpx<float>), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<cpx<df64>> h(tab.size());
+    for (size_t q = 0; q < tab.size(); ++q) h[q] = cpx<df64>{df64(tab[q].real()), df64(tab[q].imag())};
+    DQ_CUDA(cudaMalloc(&d, h.size() * sizeof(cpx<df64>)));
+    DQ_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(cpx<df64>), cudaMemcpyHostToDevice));
   }
   g_tables[key] = d;
   *out = d;
@@ -177,6 +182,7 @@ struct dqmc_ctx {
   double *Gf = nullptr;   // fresh G
   const cpx<double> *E64m = nullptr, *E64p = nullptr;
   const cpx<float> *E32m = nullptr, *E32p = nullptr;
+  const cpx<df64> *EDFm = nullptr, *EDFp = nullptr;
   std::vector<UDVd> right, left;
   UDVd tmpA, tmpB;                       // scratch UDVs for dqmc_green
   double *X = nullptr, *Xp = nullptr, *Tp = nullptr, *Dp = nullptr, *norms = nullptr;
@@ -187,15 +193,20 @@ struct dqmc_ctx {
   double *ev64 = nullptr, *evi64 = nullptr;
   float *ev32 = nullptr, *evi32 = nullptr;
   void *Gcol[2] = {nullptr, nullptr}, *Grow[2] = {nullptr, nullptr};
-  double *coef_a = nullptr, *coef_b = nullptr;  // K x K alpha / beta vectors of a block
+  double *coef_a = nullptr, *coef_b = nullptr;  // 2 x K x K alpha / beta vectors (block parity)
+  double *gnext = nullptr;                      // K x K look-ahead G[S', S'] of the next block
+  cudaStream_t side = nullptr;                  // Metropolis of the next block runs here
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void *Abuf = nullptr;                       // N x K rank-m factor A (or its FP32 pairs)
   int df_flush = 1;   // mixed: rank-m flush as double-float product (else FP64)
+  int df_prop = 1;    // mixed: FFT propagation in double-float arithmetic (else FP64)
   int stab_gemm = 2;  // mixed: stabilisation GEMMs 0 FP64, 1 double-float, 2 tensor-core digit slices
   unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
   void *ozws = nullptr;  // digit-slice workspace
   size_t ozws_bytes = 0;
   int *ozexp = nullptr;
   int *acc = nullptr, *status = nullptr;
+  uint8_t *flip_flags = nullptr;  // dqmc_replay: M x N forced-flip flags, then the M x N target
   unsigned long long *total_acc = nullptr;
   double *drift = nullptr, *drift_max = nullptr;
   double *meas_raw = nullptr, *meas_obs = nullptr;  // obs: capacity meas_cap x 6
@@ -320,9 +331,15 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
     CK(cudaMemsetAsync(c->Gcol[b], 0, (size_t)N * c->k * es, c->stream));
     CK(cudaMemsetAsync(c->Grow[b], 0, (size_t)N * c->k * es, c->stream));
   }
-  DQ_CHECK(ctx_alloc_n(c, &c->coef_a, (size_t)c->k * c->k));
-  DQ_CHECK(ctx_alloc_n(c, &c->coef_b, (size_t)c->k * c->k));
-  DQ_CHECK(ctx_alloc(c, &c->Abuf, (size_t)N * c->k * sizeof(double)));
+  DQ_CHECK(ctx_alloc_n(c, &c->coef_a, 2 * (size_t)c->k * c->k));
+  DQ_CHECK(ctx_alloc_n(c, &c->coef_b, 2 * (size_t)c->k * c->k));
+  DQ_CHECK(ctx_alloc_n(c, &c->gnext, (size_t)c->k * c->k));
+  if (!c->side) {
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
+  DQ_CHECK(ctx_alloc(c, &c->Abuf, 2 * (size_t)N * c->k * sizeof(double)));
   DQ_CHECK(ctx_alloc_n(c, &c->acc, 4));
   DQ_CHECK(ctx_alloc_n(c, &c->status, 4));
   DQ_CHECK(ctx_alloc_n(c, &c->total_acc, 1));
@@ -343,6 +360,10 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
   c->E32m = static_cast<const cpx<float> *>(t);
   DQ_CHECK(get_table(c->L, c->dtau, 1, &t));
   c->E32p = static_cast<const cpx<float> *>(t);
+  DQ_CHECK(get_table(c->L, -c->dtau, 2, &t));
+  c->EDFm = static_cast<const cpx<df64> *>(t);
+  DQ_CHECK(get_table(c->L, c->dtau, 2, &t));
+  c->EDFp = static_cast<const cpx<df64> *>(t);
 
   // measurement phases
   const int L = c->L;
@@ -419,13 +440,25 @@ dqmc_status compute_expv(dqmc_ctx *c, int l) {
   return DQMC_OK;
 }
 
+// e^{sign dtau K} on an FP64 N x N operand in place (side 0: X <- E X,
+// side 1: X <- X E), in FP64 or, in mixed precision, double-float arithmetic
+cudaError_t prop64(dqmc_ctx *c, int side, int sign, double *X, const double *pre,
+                   const double *post, const double *vscale) {
+  const int N = c->N;
+  if (c->precision == 1 && c->df_prop)
+    return launch_prop_df(c->L, side, X, X, N, N, sign < 0 ? c->EDFm : c->EDFp, pre, post, vscale,
+                          c->stream);
+  return launch_prop_f64(c->L, side, X, X, N, N, sign < 0 ? c->E64m : c->E64p, pre, post, vscale,
+                         c->stream);
+}
+
 // G <- e^{V} e^{-dtau K} G e^{+dtau K} e^{-V}
 dqmc_status wrap(dqmc_ctx *c, int l) {
   DQ_CHECK(compute_expv(c, l));
   const int N = c->N;
   if (c->precision != 2) {
-    CK(launch_prop_f64(c->L, 0, c->G64, c->G64, N, N, c->E64m, nullptr, nullptr, nullptr, c->stream));
-    CK(launch_prop_f64(c->L, 1, c->G64, c->G64, N, N, c->E64p, nullptr, c->evi64, c->ev64, c->stream));
+    CK(prop64(c, 0, -1, c->G64, nullptr, nullptr, nullptr));
+    CK(prop64(c, 1, +1, c->G64, nullptr, c->evi64, c->ev64));
   } else {
     CK(launch_prop_f32(c->L, 0, c->G32, c->G32, N, N, c->E32m, nullptr, nullptr, nullptr, c->stream));
     CK(launch_prop_f32(c->L, 1, c->G32, c->G32, N, N, c->E32p, nullptr, c->evi32, c->ev32, c->stream));
@@ -438,8 +471,8 @@ dqmc_status unwrap(dqmc_ctx *c, int l) {
   DQ_CHECK(compute_expv(c, l));
   const int N = c->N;
   if (c->precision != 2) {
-    CK(launch_prop_f64(c->L, 0, c->G64, c->G64, N, N, c->E64p, c->evi64, nullptr, c->ev64, c->stream));
-    CK(launch_prop_f64(c->L, 1, c->G64, c->G64, N, N, c->E64m, nullptr, nullptr, nullptr, c->stream));
+    CK(prop64(c, 0, +1, c->G64, c->evi64, nullptr, c->ev64));
+    CK(prop64(c, 1, -1, c->G64, nullptr, nullptr, nullptr));
   } else {
     CK(launch_prop_f32(c->L, 0, c->G32, c->G32, N, N, c->E32p, c->evi32, nullptr, c->ev32, c->stream));
     CK(launch_prop_f32(c->L, 1, c->G32, c->G32, N, N, c->E32m, nullptr, nullptr, nullptr, c->stream));
@@ -448,10 +481,17 @@ dqmc_status unwrap(dqmc_ctx *c, int l) {
 }
 
 // ---------------------------------------------------------------- delayed update of one slice
+// The blocks of one slice, pipelined over two streams. On the context's
+// stream: A = G[:, S_b] alpha_b^T, the look-ahead G'[S_{b+1}, S_{b+1}], then
+// the rank-m flush of block b (which also gathers the rows / columns of
+// block b+1). On the side stream, between the look-ahead and the next A
+// kernel: the Metropolis block b+1, so that its serial decisions overlap the
+// flush of block b. Coefficients alternate between two buffers by block parity.
 template <typename T>
-dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
+dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *forced) {
   const int N = c->N, K = c->k;
   const int nblk = (N + K - 1) / K;
+  const size_t KK = (size_t)K * K;
   T *Gc[2] = {static_cast<T *>(c->Gcol[0]), static_cast<T *>(c->Gcol[1])};
   T *Gr[2] = {static_cast<T *>(c->Grow[0]), static_cast<T *>(c->Grow[1])};
   const bool df = (c->precision == 1 && c->df_flush);
@@ -459,7 +499,6 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
   MetroArgs ma;
   ma.N = N;
   ma.K = K;
-  ma.ld_g = N;
   ma.e2l = std::exp(2.0 * c->lam);
   ma.em2l = std::exp(-2.0 * c->lam);
   ma.k0 = (uint32_t)(c->seed & 0xffffffffu);
@@ -468,12 +507,17 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
   ma.c3 = ((uint32_t)c->chain & 0xffffffu) | (kDomainMetropolis << 24);
   ma.slice0 = l - 1;
   int8_t *s = c->field + (size_t)(l - 1) * N;
+  // block 0: decisions on the context's stream from the gathered rows
+  ma.s0 = 0;
+  ma.kb = std::min(K, N);
+  ma.ld_g = N;
+  CK(launch_metropolis(ma, Gr[0], sizeof(T) == 4, s, forced, c->coef_a, c->coef_b, c->acc,
+                       c->status, c->total_acc, c->stream));
   for (int b = 0; b < nblk; ++b) {
     const int s0 = b * K, kb = std::min(K, N - s0);
-    ma.s0 = s0;
-    ma.kb = kb;
-    CK(launch_metropolis(ma, Gr[b & 1] + s0, sizeof(T) == 4, s, nullptr, c->coef_a, c->coef_b, c->acc,
-                         c->status, c->total_acc, c->stream));
+    const int par = b & 1;
+    double *al = c->coef_a + par * KK, *be = c->coef_b + par * KK;
+    int *acc = c->acc + par;
     FlushArgs fa;
     fa.N = N;
     fa.s0 = s0;
@@ -484,16 +528,32 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas) {
     fa.ldc = K;
     fa.ldb = K;
     fa.lda = K;
-    CK(launch_flush<T>(K, fa, G, Gc[b & 1], Gr[b & 1], c->coef_a, c->coef_b, c->acc, c->Abuf,
-                       Gc[(b + 1) & 1], Gr[(b + 1) & 1], df, c->stream));
+    CK(launch_amat<T>(K, fa, Gc[par], al, acc, c->Abuf, df, c->stream));
+    if (fa.nkb > 0) {
+      CK(launch_lookahead_g<T>(K, fa, G, c->Abuf, df, Gr[par], be, acc, c->gnext, c->stream));
+      CK(cudaEventRecord(c->ev_fork, c->stream));
+      CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+      MetroArgs mn = ma;
+      mn.s0 = fa.ns0;
+      mn.kb = fa.nkb;
+      mn.ld_g = fa.nkb;
+      CK(launch_metropolis(mn, c->gnext, false, s, forced ? forced + fa.ns0 : nullptr,
+                           c->coef_a + (par ^ 1) * KK, c->coef_b + (par ^ 1) * KK, c->acc + (par ^ 1),
+                           c->status, c->total_acc, c->side));
+      CK(cudaEventRecord(c->ev_join, c->side));
+    }
+    CK(launch_flush_update<T>(K, fa, G, c->Abuf, Gr[par], be, acc, Gc[par ^ 1], Gr[par ^ 1], df,
+                              c->stream));
+    if (fa.nkb > 0) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   }
   c->proposed += N;
   return DQMC_OK;
 }
 
-dqmc_status update_slice(dqmc_ctx *c, int l, int pas) {
-  return c->precision != 2 ? update_slice_t<double>(c, c->G64, l, pas)
-                           : update_slice_t<float>(c, c->G32, l, pas);
+// forced != NULL (N flags of slice l): site i flips iff forced[i] != 0
+dqmc_status update_slice(dqmc_ctx *c, int l, int pas, const uint8_t *forced = nullptr) {
+  return c->precision != 2 ? update_slice_t<double>(c, c->G64, l, pas, forced)
+                           : update_slice_t<float>(c, c->G32, l, pas, forced);
 }
 
 // ---------------------------------------------------------------- UDV stacks (FP64)
@@ -508,9 +568,9 @@ dqmc_status udv_advance(dqmc_ctx *c, const UDVd &src, UDVd &dst, const std::vect
   for (int l : slices) {
     DQ_CHECK(compute_expv(c, l));
     if (!transposed)
-      CK(launch_prop_f64(c->L, 0, c->X, c->X, N, N, c->E64m, nullptr, c->ev64, nullptr, c->stream));
+      CK(prop64(c, 0, -1, c->X, nullptr, c->ev64, nullptr));
     else
-      CK(launch_prop_f64(c->L, 0, c->X, c->X, N, N, c->E64m, c->ev64, nullptr, nullptr, c->stream));
+      CK(prop64(c, 0, -1, c->X, c->ev64, nullptr, nullptr));
   }
   // pre-pivoting: columns ordered by ||X_j|| D_j, descending
   CK(column_norms_scaled(c->X, N, src.D, c->norms, c->stream));
@@ -570,6 +630,12 @@ dqmc_status refresh(dqmc_ctx *c, int q, bool record_drift) {
     CK(convert_f64_to_f32(c->Gf, c->G32, (long)N * N, c->stream));
   }
   return DQMC_OK;
+}
+
+// flags[q] = 1 where the current spin differs from the target spin
+__global__ void flip_flags_kernel(const int8_t *field, const int8_t *target, long n, uint8_t *flags) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
+    flags[q] = field[q] != target[q] ? 1 : 0;
 }
 
 __global__ void drift_max_kernel(const double *d, double *mx) {
@@ -864,6 +930,9 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) {
   } else if (k == "df_flush") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     c->df_flush = v != 0.0;
+  } else if (k == "df_prop") {
+    if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
+    c->df_prop = v != 0.0;
   } else if (k == "gemm_sites") {
     if (v < 0 || v > 4294967295.0) return fail(DQMC_EINVAL, "gemm_sites is a 32-bit mask");
     c->gemm_sites = (unsigned)v;
@@ -1087,6 +1156,57 @@ dqmc_status dqmc_set_field(dqmc_ctx *c, const int8_t *s) {
   return ensure_ready(c);
 }
 
+dqmc_status dqmc_replay(dqmc_ctx *c, const int8_t *target, int slice, double *G_out) {
+  DQ_CHECK(check_ctx(c));
+  if (!target || !G_out) return fail(DQMC_EINVAL, "target and G_out must not be NULL");
+  if (slice < 1 || slice > c->M) return fail(DQMC_EINVAL, "slice must be in [1, M]");
+  const int N = c->N;
+  const size_t n = (size_t)c->M * N;
+  for (size_t q = 0; q < n; ++q)
+    if (target[q] != 1 && target[q] != -1) return fail(DQMC_EINVAL, "field values must be +1 or -1");
+  PhaseTimer tm(c);
+  DQ_CHECK(ensure_ready(c));
+  if (c->cur_slice != 0) return fail(DQMC_ESTATE, "replay starts at slice 0");
+  if (!c->flip_flags) DQ_CHECK(ctx_alloc_n(c, &c->flip_flags, 2 * n));
+  int8_t *tgt = reinterpret_cast<int8_t *>(c->flip_flags + n);
+  CK(cudaMemcpyAsync(tgt, target, n, cudaMemcpyHostToDevice, c->stream));
+  {
+    DQ_KSCOPE(KF_OTHER, c->stream);
+    const int grid = (int)std::min<long>(4096, ((long)n + 255) / 256);
+    flip_flags_kernel<<<grid, 256, 0, c->stream>>>(c->field, tgt, (long)n, c->flip_flags);
+    CK(cudaGetLastError());
+  }
+  GemmModeScope gm(c);
+  int q = 1;
+  for (int l = 1; l <= slice; ++l) {
+    DQ_CHECK(wrap(c, l));
+    DQ_CHECK(update_slice(c, l, 0, c->flip_flags + (size_t)(l - 1) * N));
+    c->cur_slice = l;
+    if (l == slice) break;
+    if (l == c->tau[q]) {
+      std::vector<int> sl;
+      for (int m = c->tau[q - 1] + 1; m <= c->tau[q]; ++m) sl.push_back(m);
+      DQ_CHECK(udv_advance(c, c->right[q - 1], c->right[q], sl, false));
+      DQ_CHECK(refresh(c, q, true));
+      DQ_KSCOPE(KF_OTHER, c->stream);
+      drift_max_kernel<<<1, 1, 0, c->stream>>>(c->drift, c->drift_max);
+      ++q;
+    }
+  }
+  const size_t NN = (size_t)N * N;
+  if (c->precision != 2) {
+    CK(cudaMemcpyAsync(G_out, c->G64, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    CK(convert_f32_to_f64(c->G32, c->X, (long)NN, c->stream));
+    CK(cudaMemcpyAsync(G_out, c->X, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  // the stacks no longer describe the field: the next call rebuilds them
+  c->ready = false;
+  c->cur_slice = 0;
+  return read_status(c);
+}
+
 dqmc_status dqmc_save(dqmc_ctx *c, const char *path) {
   DQ_CHECK(check_ctx(c));
   if (!path) return fail(DQMC_EINVAL, "path is NULL");
@@ -1172,6 +1292,12 @@ dqmc_status dqmc_load(dqmc_ctx *c, const char *path) {
 void dqmc_destroy(dqmc_ctx *c) {
   if (!c) return;
   if (c->allocated || !c->allocs.empty()) cudaStreamSynchronize(c->stream);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+    cudaEventDestroy(c->ev_fork);
+    cudaEventDestroy(c->ev_join);
+  }
   for (void *p : c->allocs) {
     if (c->ufree)
       c->ufree(p, c->uuser);

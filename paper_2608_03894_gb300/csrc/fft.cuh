@@ -13,7 +13,10 @@
 // exact octant reduction of the rational angle 2 pi p / q.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace dq {
 
@@ -74,13 +77,17 @@ template <int L> struct TwTable {
   double s[L];
   float cf[L];
   float sf[L];
-  constexpr TwTable() : c(), s(), cf(), sf() {
+  float cl[L];  // cf + cl = c to ~2^-48 (double-float twiddles)
+  float sl[L];
+  constexpr TwTable() : c(), s(), cf(), sf(), cl(), sl() {
     for (int j = 0; j < L; ++j) {
       const CosSin w = sincos2pi(j, L);
       c[j] = w.c;
       s[j] = w.s;
       cf[j] = (float)w.c;
       sf[j] = (float)w.s;
+      cl[j] = (float)(w.c - (double)cf[j]);
+      sl[j] = (float)(w.s - (double)sf[j]);
     }
   }
 };
@@ -89,10 +96,14 @@ template <int L> __constant__ TwTable<L> kTw = TwTable<L>();
 
 template <typename T, int L> struct Tw {
   static __device__ __forceinline__ T c(int e) {
-    if constexpr (sizeof(T) == 8) return kTw<L>.c[e]; else return kTw<L>.cf[e];
+    if constexpr (std::is_same<T, df64>::value) return df64(kTw<L>.cf[e], kTw<L>.cl[e]);
+    else if constexpr (sizeof(T) == 8) return kTw<L>.c[e];
+    else return kTw<L>.cf[e];
   }
   static __device__ __forceinline__ T s(int e) {
-    if constexpr (sizeof(T) == 8) return kTw<L>.s[e]; else return kTw<L>.sf[e];
+    if constexpr (std::is_same<T, df64>::value) return df64(kTw<L>.sf[e], kTw<L>.sl[e]);
+    else if constexpr (sizeof(T) == 8) return kTw<L>.s[e];
+    else return kTw<L>.sf[e];
   }
 };
 

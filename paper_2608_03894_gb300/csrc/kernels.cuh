@@ -3,6 +3,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "df64.cuh"
 
 namespace dq {
 
@@ -13,6 +14,11 @@ cudaError_t launch_prop_f64(int L, int side, const double *X, double *Y, int nve
 cudaError_t launch_prop_f32(int L, int side, const float *X, float *Y, int nvec, int ld,
                             const cpx<float> *E, const float *pre, const float *post,
                             const float *vscale, cudaStream_t st);
+
+// FP64 operand, double-float arithmetic (prop_df.cu); E: (hi, lo) FP32 pairs
+cudaError_t launch_prop_df(int L, int side, const double *X, double *Y, int nvec, int ld,
+                           const cpx<df64> *E, const double *pre, const double *post,
+                           const double *vscale, cudaStream_t st);
 
 // ---- delayed update (update.cu)
 template <typename T>
@@ -43,12 +49,28 @@ struct FlushArgs {
   int lda;         // row stride of alpha
 };
 // G <- G - (Gcol alpha^T)(beta (E_S - Grow)): the A kernel then the rank-m
-// flush. Abuf: N x K scratch (T, or float2 pairs when df). df = FP64-accurate
-// double-float product on the FP32 units (T = double only).
+// flush. Abuf: N x K scratch (T), or, when df, 2 N K float2 pairs (A, then B).
+// df = FP64-accurate double-float product on the FP32 units (T = double only).
 template <typename T>
 cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
                          const double *alpha, const double *beta, const int *acc, void *Abuf,
                          T *Gcol_next, T *Grow_next, bool df, cudaStream_t st);
+
+// The two halves of launch_flush: A = Gcol alpha^T into Abuf, then the
+// rank-m update of G (with the next block's gather when a.nkb > 0).
+template <typename T>
+cudaError_t launch_amat(int K, const FlushArgs &a, const T *Gcol, const double *alpha,
+                        const int *acc, void *Abuf, bool df, cudaStream_t st);
+template <typename T>
+cudaError_t launch_flush_update(int K, const FlushArgs &a, T *G, const void *Abuf, const T *Grow,
+                                const double *beta, const int *acc, T *Gcol_next, T *Grow_next,
+                                bool df, cudaStream_t st);
+// Look-ahead: the next block's G'[S', S'] (a.nkb x a.nkb doubles, row stride
+// a.nkb) after the pending flush, from the pre-flush G, A (Abuf) and beta.
+template <typename T>
+cudaError_t launch_lookahead_g(int K, const FlushArgs &a, const T *G, const void *Abuf, bool df,
+                               const T *Grow, const double *beta, const int *acc, double *gnext,
+                               cudaStream_t st);
 
 // ---- measurement (measure.cu)
 struct MeasTables {

@@ -11,6 +11,7 @@
 #include <cooperative_groups.h>
 
 #include "linalg.cuh"
+#include "kernels.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -181,56 +182,99 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
 }
 
 // ====================================================================== QR panel
-constexpr int kClusterCTAs = 8;
+// The panel runs on one thread-block cluster: 16 CTAs (non-portable size)
+// when the device co-schedules such a cluster with the panel's shared
+// memory, else 8. FP64 issue rate per SM is low on this part, so the cluster
+// is made as wide as possible and the panel kernel does only the column
+// loop; the Gram matrix V^T V, the T factor and every product with V run as
+// GEMMs over the whole GPU.
+static int g_qr_ctas = 0;
 
-int qr_panel_width(int n) {
-  // nb = 64 when a 1/8 slice of the panel rows plus the nb x nb Gram/T
-  // buffers fit in shared memory, else 32
-  const int rows_per = (n + kClusterCTAs - 1) / kClusterCTAs;
-  const size_t need64 = ((size_t)rows_per * 65 + 3 * 64 * 64 + 16 * 64 + 64) * sizeof(double);
-  return need64 <= 220 * 1024 ? 64 : 32;
+static size_t qr_panel_smem_rows(int rows_per, int nb) {
+  return ((size_t)rows_per * (nb + 1) + 16 * (size_t)nb + 64) * sizeof(double);
 }
 
-static size_t qr_panel_smem(int n, int nb) {
-  const int rows_per = (n + kClusterCTAs - 1) / kClusterCTAs;
-  return ((size_t)rows_per * (nb + 1) + 3 * (size_t)nb * nb + 16 * (size_t)nb + 64) * sizeof(double);
+template <int NB> __global__ void qr_panel_kernel(double *, int, int, int, double *, double *);
+
+static int qr_cluster_ctas() {
+  if (g_qr_ctas) return g_qr_ctas;
+  int ctas = 8;
+  const int want = 16;
+  if (cudaFuncSetAttribute(qr_panel_kernel<64>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(qr_panel_kernel<32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess) {
+    // the largest panel used here (L = 36, N = 3888) with nb = 64
+    const size_t smem = qr_panel_smem_rows((3888 + want - 1) / want, 64);
+    if (cudaFuncSetAttribute(qr_panel_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(want);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = want;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, qr_panel_kernel<64>, &cfg) == cudaSuccess &&
+          nclusters >= 1)
+        ctas = want;
+    }
+  }
+  cudaGetLastError();  // a refused query leaves no sticky error; clear the last one
+  g_qr_ctas = ctas;
+  return ctas;
+}
+
+int qr_panel_width(int n) {
+  // nb = 64 when one CTA's share of the panel rows fits in shared memory, else 32
+  const int ctas = qr_cluster_ctas();
+  const int rows_per = (n + ctas - 1) / ctas;
+  return qr_panel_smem_rows(rows_per, 64) <= 220 * 1024 ? 64 : 32;
 }
 
 size_t qr_work_doubles(int n) {
   const int nb = qr_panel_width(n);
   const int nblk = (n + nb - 1) / nb;
-  return 3 * (size_t)n * n + (size_t)n + (size_t)nb * n + (size_t)nblk * nb * nb;
+  // V, tau, W, W2, Gram, T blocks, Rinv blocks
+  return (size_t)n * n + (size_t)n + 2 * (size_t)nb * n + (size_t)nb * nb +
+         2 * (size_t)nblk * nb * nb;
 }
 
 void qr_work_bind(QRWork &w, int n, double *mem) {
   w.n = n;
   w.nb = qr_panel_width(n);
+  w.ctas = qr_cluster_ctas();
   const int nblk = (n + w.nb - 1) / w.nb;
   w.V = mem;
-  w.Y = w.V + (size_t)n * n;
-  w.Y2 = w.Y + (size_t)n * n;
-  w.tau = w.Y2 + (size_t)n * n;
+  w.tau = w.V + (size_t)n * n;
   w.W = w.tau + n;
-  w.Rinv = w.W + (size_t)w.nb * n;
-  (void)nblk;
+  w.W2 = w.W + (size_t)w.nb * n;
+  w.Gram = w.W2 + (size_t)w.nb * n;
+  w.T = w.Gram + (size_t)w.nb * w.nb;
+  w.Rinv = w.T + (size_t)nblk * w.nb * w.nb;
 }
 
 // Factorises the panel A[p:n, p:p+nc] (nc <= NB) in place. Rows are split
-// over the 8 CTAs of the cluster; CTA r owns panel rows [r R, (r+1) R).
+// over the CTAs of the cluster; CTA r owns panel rows [r R, (r+1) R).
 // Per column jj: every CTA forms partial dot products of the column with the
 // remaining panel columns over its rows, the cluster combines them through
 // DSMEM, every CTA computes the same reflector (LAPACK convention:
 // H = I - tau v v^T, v_0 = 1, H x = beta e_1) and updates its own rows.
-// Afterwards: V explicit, T from the Gram matrix V^T V by the standard
-// recurrence, Y = V T^T and Y2 = V T.
+// Output: R and the reflectors in A, V explicit (unit lower trapezoidal,
+// zeros above) and tau.
 template <int NB>
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
-    qr_panel_kernel(double *A, int n, int p, int nc, double *V, double *Y, double *Y2,
-                    double *tau_out) {
+__global__ void __launch_bounds__(256)
+    qr_panel_kernel(double *A, int n, int p, int nc, double *V, double *tau_out) {
   cg::cluster_group cluster = cg::this_cluster();
+  const int ncta = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int m = n - p;
-  const int rows_per = (m + kClusterCTAs - 1) / kClusterCTAs;
+  const int rows_per = (m + ncta - 1) / ncta;
   const int lr0 = rank * rows_per;
   const int myrows = max(0, min(m, lr0 + rows_per) - lr0);
   constexpr int LDP = NB + 1;
@@ -243,9 +287,6 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
   double *sy0 = sD + NB;                     // NB
   double *sw = sy0 + NB;                     // NB
   double *stau = sw + NB;                    // NB
-  double *Gm = stau + NB;                    // NB x NB (partial Gram)
-  double *Gs = Gm + NB * NB;                 // NB x NB (summed Gram, rank 0)
-  double *Tm = Gs + NB * NB;                 // NB x NB (T)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int e = tid; e < myrows * NB; e += 256) {
@@ -274,10 +315,13 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
       for (int w = 0; w < 8; ++w) s += red[w * NB + tid];
       part[buf * NB + tid] = s;
     }
+    // the partial sums and the owner's pivot row become visible cluster-wide;
+    // a CTA can only reuse this buffer parity after the next cluster barrier,
+    // which every CTA reaches after its reads below
     cluster.sync();
     if (tid < NB) {
       double D = 0.0;
-      for (int r2 = 0; r2 < kClusterCTAs; ++r2) {
+      for (int r2 = 0; r2 < ncta; ++r2) {
         const double *rp = cluster.map_shared_rank(part, r2);
         D += rp[buf * NB + tid];
       }
@@ -313,7 +357,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     __syncthreads();
   }
 
-  // write back R / V into A, explicit V, and the partial Gram V^T V
+  // write back R / V into A and the explicit V
   for (int e = tid; e < myrows * nc; e += 256) {
     const int r = e / nc, c = e % nc;
     const int lr = lr0 + r;
@@ -321,73 +365,85 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     A[(size_t)(p + lr) * n + p + c] = pv;
     V[(size_t)(p + lr) * n + p + c] = (lr > c) ? pv : (lr == c ? 1.0 : 0.0);
   }
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int a = e / NB, b = e % NB;
-    double acc = 0.0;
-    if (a < nc && b < nc) {
-      for (int r = 0; r < myrows; ++r) {
-        const int lr = lr0 + r;
-        const double va = (lr > a) ? P[r * LDP + a] : (lr == a ? 1.0 : 0.0);
-        const double vb = (lr > b) ? P[r * LDP + b] : (lr == b ? 1.0 : 0.0);
-        acc = fma(va, vb, acc);
-      }
-    }
-    Gm[e] = acc;
-  }
-  cluster.sync();
-  if (rank == 0) {
-    for (int e = tid; e < NB * NB; e += 256) {
-      double s = 0.0;
-      for (int r2 = 0; r2 < kClusterCTAs; ++r2) s += cluster.map_shared_rank(Gm, r2)[e];
-      Gs[e] = s;
-      Tm[e] = 0.0;
-    }
-    __syncthreads();
-    // T upper triangular: T_jj = tau_j, T[0:j, j] = -tau_j T[0:j,0:j] Gram[0:j, j]
-    for (int j = 0; j < nc; ++j) {
-      if (tid < j) {
-        double acc = 0.0;
-        for (int k = tid; k < j; ++k) acc = fma(Tm[tid * NB + k], Gs[k * NB + j], acc);
-        Tm[tid * NB + j] = -stau[j] * acc;
-      }
-      if (tid == j) Tm[j * NB + j] = stau[j];
-      __syncthreads();
-    }
+  if (rank == 0)
     for (int j = tid; j < nc; j += 256) tau_out[p + j] = stau[j];
-  }
+  // no CTA leaves while another may still read its shared memory
   cluster.sync();
-  if (rank != 0) {
-    const double *T0 = cluster.map_shared_rank(Tm, 0);
-    for (int e = tid; e < NB * NB; e += 256) Tm[e] = T0[e];
-  }
+}
+
+// T (nc x nc, upper triangular, leading dimension NB) of the compact WY form
+// H_0 H_1 ... H_{nc-1} = I - V T V^T from the Gram matrix V^T V and tau:
+// T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V^T V)[0:j, j]. One CTA.
+__global__ void qr_t_kernel(const double *Gram, int ldg, const double *tau, int nc, int NB,
+                            double *T) {
+  extern __shared__ double st[];  // NB x NB
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += blockDim.x) st[e] = 0.0;
   __syncthreads();
-  // Y = V T^T, Y2 = V T for my rows
-  for (int e = tid; e < myrows * nc; e += 256) {
-    const int r = e / nc, a = e % nc;
-    const int lr = lr0 + r;
-    double y = 0.0, y2 = 0.0;
-    for (int b = 0; b < nc; ++b) {
-      const double vb = (lr > b) ? P[r * LDP + b] : (lr == b ? 1.0 : 0.0);
-      y = fma(vb, Tm[a * NB + b], y);
-      y2 = fma(vb, Tm[b * NB + a], y2);
+  for (int j = 0; j < nc; ++j) {
+    if (tid < j) {
+      double acc = 0.0;
+      for (int k = tid; k < j; ++k) acc = fma(st[tid * NB + k], Gram[(size_t)k * ldg + j], acc);
+      st[tid * NB + j] = -tau[j] * acc;
     }
-    Y[(size_t)(p + lr) * n + p + a] = y;
-    Y2[(size_t)(p + lr) * n + p + a] = y2;
+    if (tid == j) st[j * NB + j] = tau[j];
+    __syncthreads();
   }
-  cluster.sync();
+  for (int e = tid; e < NB * NB; e += blockDim.x) T[e] = st[e];
 }
 
 template <int NB>
 static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, cudaStream_t st) {
-  const size_t smem = qr_panel_smem(n, NB);
-  cudaError_t e = cudaFuncSetAttribute(qr_panel_kernel<NB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int ctas = w.ctas;
+  const int rows_per = (n - p + ctas - 1) / ctas;
+  const size_t smem = qr_panel_smem_rows(rows_per, NB);
+  cudaError_t e = ensure_smem_attr((const void *)qr_panel_kernel<NB>,
+                                   (int)qr_panel_smem_rows((n + ctas - 1) / ctas, NB));
   if (e != cudaSuccess) return e;
-  DQ_KSCOPE(KF_QRPANEL, st);
-  // Householder panel: ~4 m nc^2 flops; the m x nc panel read and written once
-  add_work(KF_QRPANEL, 4.0 * (n - p) * (double)nc * nc, 16.0 * (n - p) * (double)nc);
-  qr_panel_kernel<NB><<<kClusterCTAs, 256, smem, st>>>(A, n, p, nc, w.V, w.Y, w.Y2, w.tau);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = ctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  {
+    DQ_KSCOPE(KF_QRPANEL, st);
+    // Householder column loop: ~2 m nc^2 flops; the m x nc panel read and written once
+    add_work(KF_QRPANEL, 2.0 * (n - p) * (double)nc * nc, 16.0 * (n - p) * (double)nc);
+    e = cudaLaunchKernelEx(&cfg, qr_panel_kernel<NB>, A, n, p, nc, w.V, w.tau);
+    if (e != cudaSuccess) return e;
+  }
+  // Gram = V_p^T V_p, then T_p
+  const int m = n - p;
+  e = dgemm(true, false, nc, nc, m, 1.0, w.V + (size_t)p * n + p, n, w.V + (size_t)p * n + p, n, 0.0,
+            w.Gram, w.nb, nullptr, nullptr, st);
+  if (e != cudaSuccess) return e;
+  DQ_KSCOPE(KF_OTHER, st);
+  qr_t_kernel<<<1, 64, (size_t)w.nb * w.nb * sizeof(double), st>>>(w.Gram, w.nb, w.tau + p, nc, w.nb,
+                                                                   w.T + (size_t)(p / w.nb) * w.nb * w.nb);
   return cudaGetLastError();
+}
+
+// B[p:, 0:ncols] <- (I - V_p op(T_p) V_p^T) B[p:, 0:ncols], op = T^T (Q^T side) or T (Q side)
+static cudaError_t apply_block_reflector(const QRWork &w, int p, int nc, bool trans_t, double *B,
+                                         int ldb, int ncols, cudaStream_t st) {
+  const int n = w.n, m = n - p;
+  const double *Vp = w.V + (size_t)p * n + p;
+  const double *Tp = w.T + (size_t)(p / w.nb) * w.nb * w.nb;
+  cudaError_t e = dgemm(true, false, nc, ncols, m, 1.0, Vp, n, B, ldb, 0.0, w.W, ncols, nullptr,
+                        nullptr, st);
+  if (e != cudaSuccess) return e;
+  e = dgemm(trans_t, false, nc, ncols, nc, 1.0, Tp, w.nb, w.W, ncols, 0.0, w.W2, ncols, nullptr,
+            nullptr, st);
+  if (e != cudaSuccess) return e;
+  return dgemm(false, false, m, ncols, nc, -1.0, Vp, n, w.W2, ncols, 1.0, B, ldb, nullptr, nullptr,
+               st, 1);
 }
 
 cudaError_t qr_factor(double *A, int n, QRWork &w, cudaStream_t st) {
@@ -399,13 +455,8 @@ cudaError_t qr_factor(double *A, int n, QRWork &w, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const int ntr = n - p - nc;
     if (ntr > 0) {
-      // W = V_p^T A[p:, p+nc:]  (nc x ntr, K = n - p)
-      e = dgemm(true, false, nc, ntr, n - p, 1.0, w.V + (size_t)p * n + p, n,
-                A + (size_t)p * n + p + nc, n, 0.0, w.W, ntr, nullptr, nullptr, st);
-      if (e != cudaSuccess) return e;
-      // A[p:, p+nc:] -= Y_p W
-      e = dgemm(false, false, n - p, ntr, nc, -1.0, w.Y + (size_t)p * n + p, n, w.W, ntr, 1.0,
-                A + (size_t)p * n + p + nc, n, nullptr, nullptr, st, 1);
+      // A[p:, p+nc:] <- H^T A[p:, p+nc:] = (I - V T^T V^T) A[p:, p+nc:]
+      e = apply_block_reflector(w, p, nc, true, A + (size_t)p * n + p + nc, n, ntr, st);
       if (e != cudaSuccess) return e;
     }
   }
@@ -419,12 +470,8 @@ cudaError_t qr_form_q(double *Q, int n, QRWork &w, cudaStream_t st) {
   const int last = ((n - 1) / nb) * nb;
   for (int p = last; p >= 0; p -= nb) {
     const int nc = min(nb, n - p);
-    const int cols = n - p;
-    e = dgemm(true, false, nc, cols, n - p, 1.0, w.V + (size_t)p * n + p, n,
-              Q + (size_t)p * n + p, n, 0.0, w.W, cols, nullptr, nullptr, st);
-    if (e != cudaSuccess) return e;
-    e = dgemm(false, false, n - p, cols, nc, -1.0, w.Y2 + (size_t)p * n + p, n, w.W, cols, 1.0,
-              Q + (size_t)p * n + p, n, nullptr, nullptr, st, 1);
+    // Q[p:, p:] <- (I - V T V^T) Q[p:, p:]  (Q = H_0 H_1 ... applied right to left)
+    e = apply_block_reflector(w, p, nc, false, Q + (size_t)p * n + p, n, n - p, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -434,11 +481,7 @@ cudaError_t qr_apply_qt(double *B, int n, int ncols, int ldb, QRWork &w, cudaStr
   const int nb = w.nb;
   for (int p = 0; p < n; p += nb) {
     const int nc = min(nb, n - p);
-    cudaError_t e = dgemm(true, false, nc, ncols, n - p, 1.0, w.V + (size_t)p * n + p, n,
-                          B + (size_t)p * ldb, ldb, 0.0, w.W, ncols, nullptr, nullptr, st);
-    if (e != cudaSuccess) return e;
-    e = dgemm(false, false, n - p, ncols, nc, -1.0, w.Y + (size_t)p * n + p, n, w.W, ncols, 1.0,
-              B + (size_t)p * ldb, ldb, nullptr, nullptr, st, 1);
+    cudaError_t e = apply_block_reflector(w, p, nc, true, B + (size_t)p * ldb, ldb, ncols, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

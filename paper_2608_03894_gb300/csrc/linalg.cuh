@@ -54,11 +54,13 @@ void set_gemm_site_mask(unsigned mask);
 cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st);
 
 // Householder QR workspace for an n x n matrix: V (unit lower trapezoidal,
-// explicit), Y = V T^T and Y2 = V T per panel (panel p in columns p..p+nb),
-// tau, and the inverses of the nb x nb diagonal blocks of R.
+// explicit; panel p in columns p..p+nb), tau, the compact-WY factor T of each
+// panel (nb x nb, upper triangular), GEMM scratch W / W2 (nb x n) and the
+// panel Gram matrix, and the inverses of the nb x nb diagonal blocks of R.
 struct QRWork {
-  int n = 0, nb = 0;
-  double *V = nullptr, *Y = nullptr, *Y2 = nullptr, *tau = nullptr, *W = nullptr;
+  int n = 0, nb = 0, ctas = 8;
+  double *V = nullptr, *tau = nullptr, *W = nullptr, *W2 = nullptr, *Gram = nullptr;
+  double *T = nullptr;     // (n/nb + 1) blocks of nb x nb
   double *Rinv = nullptr;  // (n/nb + 1) blocks of nb x nb
 };
 int qr_panel_width(int n);

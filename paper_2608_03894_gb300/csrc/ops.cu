@@ -34,9 +34,14 @@ static dqmc_status op_table(int L, double scale, int prec, const void **out) {
     for (size_t q = 0; q < tab.size(); ++q) h[q] = cpx<double>{tab[q].real(), tab[q].imag()};
     DQ_CUDA(cudaMalloc(&d, h.size() * sizeof(h[0])));
     DQ_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice));
-  } else {
+  } else if (prec == 1) {
     std::vector<cpx<float>> h(tab.size());
     for (size_t q = 0; q < tab.size(); ++q) h[q] = cpx<float>{(float)tab[q].real(), (float)tab[q].imag()};
+    DQ_CUDA(cudaMalloc(&d, h.size() * sizeof(h[0])));
+    DQ_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<cpx<df64>> h(tab.size());
+    for (size_t q = 0; q < tab.size(); ++q) h[q] = cpx<df64>{df64(tab[q].real()), df64(tab[q].imag())};
     DQ_CUDA(cudaMalloc(&d, h.size() * sizeof(h[0])));
     DQ_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice));
   }
@@ -69,6 +74,17 @@ dqmc_status dqmc_op_propagate_f64(int L, double scale, int side, const double *X
   DQ_CHECK(op_table(L, scale, 0, &E));
   DQ_CUDA(launch_prop_f64(L, side, X, Y, nvec, ld, static_cast<const cpx<double> *>(E), pre, post,
                           vscale, static_cast<cudaStream_t>(stream)));
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_op_propagate_df(int L, double scale, int side, const double *X, double *Y,
+                                 int nvec, int ld, const double *pre, const double *post,
+                                 const double *vscale, void *stream) {
+  DQ_CHECK(check_prop(L, side, X, Y, nvec, ld));
+  const void *E = nullptr;
+  DQ_CHECK(op_table(L, scale, 2, &E));
+  DQ_CUDA(launch_prop_df(L, side, X, Y, nvec, ld, static_cast<const cpx<df64> *>(E), pre, post,
+                         vscale, static_cast<cudaStream_t>(stream)));
   return DQMC_OK;
 }
 
@@ -124,9 +140,9 @@ static dqmc_status op_flush(int N, int site0, int kb, T *G, const T *Gcol, const
   int K = 4;
   while (K < kb) K <<= 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // scratch for the N x K factor A, stream-ordered
+  // scratch for the N x K factor A (and, double-float, the K x N factor B), stream-ordered
   void *Abuf = nullptr;
-  DQ_CUDA(cudaMallocAsync(&Abuf, (size_t)N * K * 8, st));
+  DQ_CUDA(cudaMallocAsync(&Abuf, (size_t)N * K * 8 * (df ? 2 : 1), st));
   FlushArgs a{N, site0, kb, 0, 0, 0, kb, kb, kb};
   cudaError_t e = launch_flush<T>(K, a, G, Gcol, Grow, alpha, beta, accept_count, Abuf, nullptr,
                                   nullptr, df, st);

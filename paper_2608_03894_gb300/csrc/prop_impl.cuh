@@ -24,6 +24,20 @@
 
 namespace dq {
 
+// Storage type of the operand in HBM for compute type T: double-float
+// (df64) computes on FP64 data, the others store what they compute.
+template <typename T> struct PropStore { using type = T; };
+template <> struct PropStore<df64> { using type = double; };
+
+template <typename T, typename S> __device__ __forceinline__ T ld_val(S x) {
+  if constexpr (std::is_same<T, df64>::value) return df_from(x);
+  else return x;
+}
+template <typename S, typename T> __device__ __forceinline__ S st_val(T x) {
+  if constexpr (std::is_same<T, df64>::value) return df_to(x);
+  else return x;
+}
+
 template <typename T, int L> struct PropCfg {
   static constexpr int H = L / 2 + 1;
   static constexpr int N = 3 * L * L;
@@ -43,10 +57,13 @@ template <typename T, int L> struct PropCfg {
 
 template <typename T, int L, int SIDE>
 __global__ void __launch_bounds__(256)
-    prop_kernel(const T *__restrict__ X, T *__restrict__ Y, int nvec, int ld,
-                const cpx<T> *__restrict__ E, const T *__restrict__ pre,
-                const T *__restrict__ post, const T *__restrict__ vscale) {
+    prop_kernel(const typename PropStore<T>::type *__restrict__ X,
+                typename PropStore<T>::type *__restrict__ Y, int nvec, int ld,
+                const cpx<T> *__restrict__ E, const typename PropStore<T>::type *__restrict__ pre,
+                const typename PropStore<T>::type *__restrict__ post,
+                const typename PropStore<T>::type *__restrict__ vscale) {
   using C = PropCfg<T, L>;
+  using S = typename PropStore<T>::type;
   constexpr int H = C::H, N = C::N, VT = C::VT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smem_raw);
@@ -61,8 +78,8 @@ __global__ void __launch_bounds__(256)
       const int v = w % VT, i = w / VT;
       T val = T(0);
       if (v < nv) {
-        val = X[(size_t)i * ld + v0 + v];
-        if (pre) val *= pre[i];
+        val = ld_val<T, S>(X[(size_t)i * ld + v0 + v]);
+        if (pre) val *= ld_val<T, S>(pre[i]);
       }
       const int a = i % 3, cell = i / 3, x2 = cell % L, x1 = cell / L;
       rbuf[2 * (((a * L + x1) * H + (x2 >> 1)) * VT + v) + (x2 & 1)] = val;
@@ -72,8 +89,8 @@ __global__ void __launch_bounds__(256)
       const int j = w % N, v = w / N;
       T val = T(0);
       if (v < nv) {
-        val = X[(size_t)(v0 + v) * ld + j];
-        if (pre) val *= pre[j];
+        val = ld_val<T, S>(X[(size_t)(v0 + v) * ld + j]);
+        if (pre) val *= ld_val<T, S>(pre[j]);
       }
       const int a = j % 3, cell = j / 3, x2 = cell % L, x1 = cell / L;
       rbuf[2 * (((a * L + x1) * H + (x2 >> 1)) * VT + v) + (x2 & 1)] = val;
@@ -187,9 +204,9 @@ __global__ void __launch_bounds__(256)
       if (v >= nv) continue;
       const int a = i % 3, cell = i / 3, x2 = cell % L, x1 = cell / L;
       T val = rbuf[2 * (((a * L + x1) * H + (x2 >> 1)) * VT + v) + (x2 & 1)];
-      if (post) val *= post[i];
-      if (vscale) val *= vscale[v0 + v];
-      Y[(size_t)i * ld + v0 + v] = val;
+      if (post) val *= ld_val<T, S>(post[i]);
+      if (vscale) val *= ld_val<T, S>(vscale[v0 + v]);
+      Y[(size_t)i * ld + v0 + v] = st_val<S, T>(val);
     }
   } else {
     for (int w = tid; w < N * VT; w += blockDim.x) {
@@ -197,17 +214,20 @@ __global__ void __launch_bounds__(256)
       if (v >= nv) continue;
       const int a = j % 3, cell = j / 3, x2 = cell % L, x1 = cell / L;
       T val = rbuf[2 * (((a * L + x1) * H + (x2 >> 1)) * VT + v) + (x2 & 1)];
-      if (post) val *= post[j];
-      if (vscale) val *= vscale[v0 + v];
-      Y[(size_t)(v0 + v) * ld + j] = val;
+      if (post) val *= ld_val<T, S>(post[j]);
+      if (vscale) val *= ld_val<T, S>(vscale[v0 + v]);
+      Y[(size_t)(v0 + v) * ld + j] = st_val<S, T>(val);
     }
   }
 }
 
 // Host launcher for one L (templated) -- returns cudaError_t of the launch.
 template <typename T, int L>
-cudaError_t launch_prop_L(int side, const T *X, T *Y, int nvec, int ld, const cpx<T> *E,
-                          const T *pre, const T *post, const T *vscale, cudaStream_t st) {
+cudaError_t launch_prop_L(int side, const typename PropStore<T>::type *X,
+                          typename PropStore<T>::type *Y, int nvec, int ld, const cpx<T> *E,
+                          const typename PropStore<T>::type *pre,
+                          const typename PropStore<T>::type *post,
+                          const typename PropStore<T>::type *vscale, cudaStream_t st) {
   using C = PropCfg<T, L>;
   const int grid = (nvec + C::VT - 1) / C::VT;
   if (grid == 0) return cudaSuccess;
@@ -217,7 +237,8 @@ cudaError_t launch_prop_L(int side, const T *X, T *Y, int nvec, int ld, const cp
   {
     const double L2 = (double)L * L;
     const double lg = L > 1 ? std::log2(L2) : 0.0;
-    add_work(KF_PROP, (15.0 * L2 * lg + 36.0 * L2) * nvec, 2.0 * C::N * (double)nvec * sizeof(T));
+    add_work(KF_PROP, (15.0 * L2 * lg + 36.0 * L2) * nvec,
+             2.0 * C::N * (double)nvec * sizeof(typename PropStore<T>::type));
   }
   if (side == 0) {
     cudaError_t e = ensure_smem_attr((const void *)prop_kernel<T, L, 0>, C::kSmem);
@@ -232,8 +253,11 @@ cudaError_t launch_prop_L(int side, const T *X, T *Y, int nvec, int ld, const cp
 }
 
 template <typename T>
-cudaError_t launch_prop(int L, int side, const T *X, T *Y, int nvec, int ld, const cpx<T> *E,
-                        const T *pre, const T *post, const T *vscale, cudaStream_t st) {
+cudaError_t launch_prop(int L, int side, const typename PropStore<T>::type *X,
+                        typename PropStore<T>::type *Y, int nvec, int ld, const cpx<T> *E,
+                        const typename PropStore<T>::type *pre,
+                        const typename PropStore<T>::type *post,
+                        const typename PropStore<T>::type *vscale, cudaStream_t st) {
   switch (L) {
 #define DQ_PROP_CASE(LL) \
   case LL: return launch_prop_L<T, LL>(side, X, Y, nvec, ld, E, pre, post, vscale, st);

@@ -20,46 +20,10 @@
 // G[:,S'] and G[S',:] of the next block.
 #include <type_traits>
 
+#include "df64.cuh"
 #include "kernels.cuh"
 
 namespace dq {
-
-// ----------------------------------------------------------------- FP64 <-> FP32 pairs
-// Split x into hi + lo (FP32) with integer operations only (the FP64 pipe is
-// 1/64 of the FP32 rate on GB300): hi carries the top 24 significand bits of
-// x (truncated), lo the next 24 of the remaining 29 (rounded by the integer
-// to FP32 conversion): |x - hi - lo| <= 2^-47 |x|. Values outside the FP32
-// normal range map to 0 (|x| < 2^-126) or +-inf.
-__device__ __forceinline__ float2 split_df_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(b >> 63) << 31;
-  const int e = (int)((b >> 52) & 0x7ff);
-  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-  const int e32 = e - 1023 + 127;
-  if (e32 <= 0) return make_float2(0.f, 0.f);
-  if (e32 >= 255) return make_float2(__int_as_float(sign | 0x7f800000u), 0.f);
-  const float hi = __int_as_float(sign | ((unsigned int)e32 << 23) | (unsigned int)(mant >> 29));
-  const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull);  // 29 bits, weight 2^(e-1075)
-  const int el = e - 1075 + 127;                                 // FP32 exponent of 2^(e-1075)
-  float lo = 0.f;
-  if (rem != 0u && el > 0) {
-    lo = __uint2float_rn(rem) * __int_as_float((unsigned int)el << 23);
-    if (sign) lo = -lo;
-  }
-  return make_float2(hi, lo);
-}
-
-// FP32 -> FP64 by re-biasing the exponent (integer operations only); FP32
-// subnormals map to 0.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned int b = (unsigned int)__float_as_int(f);
-  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
-  const unsigned int e = (b >> 23) & 0xff;
-  if (e == 0) return __longlong_as_double((long long)sign);
-  const unsigned long long e11 = (e == 255) ? 2047ull : (unsigned long long)(e + 896);
-  const unsigned long long mant = (unsigned long long)(b & 0x7fffff) << 29;
-  return __longlong_as_double((long long)(sign | (e11 << 52) | mant));
-}
 
 // ----------------------------------------------------------------- gather
 // Gcol[i*K + t] = G[i, s0 + t] (t < kb, zero for kb <= t < K),
@@ -384,21 +348,166 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <typename T, int K, bool DF>
-static cudaError_t launch_flush_K(const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
-                                  const double *alpha, const double *beta, const int *acc,
-                                  void *Abuf, T *Gcol_next, T *Grow_next, cudaStream_t st) {
-  {
-    const int rows_per = 256 / K;
-    DQ_KSCOPE(KF_OTHER, st);
-    add_work(KF_OTHER, 2.0 * a.N * (double)a.kb * a.kb, 8.0 * a.N * (double)(a.kb + K));
-    if constexpr (DF)
-      amat_kernel<T, float2><<<(a.N + rows_per - 1) / rows_per, 256, 0, st>>>(
-          a.N, K, a.kb, a.ldc, Gcol, alpha, a.lda, acc, static_cast<float2 *>(Abuf));
-    else
-      amat_kernel<T, T><<<(a.N + rows_per - 1) / rows_per, 256, 0, st>>>(
-          a.N, K, a.kb, a.ldc, Gcol, alpha, a.lda, acc, static_cast<T *>(Abuf));
+// ----------------------------------------------------------------- tiled double-float flush
+// B[mm][j] = beta[mm][j - s0] [j in S] - sum_w beta[mm][w] Grow[w][j] for
+// mm < m (zero rows above), computed once per column in FP64 and stored as
+// (hi, lo) FP32 pairs, K x N row-major.
+__global__ void __launch_bounds__(256)
+    bmat_df_kernel(FlushArgs a, int K, const double *__restrict__ Grow,
+                   const double *__restrict__ beta, const int *__restrict__ accept_count,
+                   float2 *__restrict__ B) {
+  const int N = a.N;
+  const int j = blockIdx.x * 256 + threadIdx.x, mm = blockIdx.y;
+  if (j >= N) return;
+  const int m = accept_count ? *accept_count : a.kb;
+  double w = 0.0;
+  if (mm < m) {
+    const int js = j - a.s0;
+    if (js >= 0 && js < a.kb) w = beta[mm * a.ldb + js];
+    for (int u = 0; u < a.kb; ++u) w = fma(-beta[mm * a.ldb + u], Grow[(size_t)u * N + j], w);
   }
+  B[(size_t)mm * N + j] = split_df_bits(w);
+}
+
+// G[i0:i0+64, j0:j0+64] -= A B with A (N x K) and B (K x N) as FP32 pairs:
+// one 64 x 64 tile per CTA, 256 threads, a 4 x 4 block of outputs per thread
+// (rows 4 ty .. 4 ty + 3, columns 4 tx .. 4 tx + 3), operands staged once in
+// shared memory (A transposed, row stride 66 pairs). Abuf holds A (N x K
+// pairs) followed by B (K x N pairs). Each MAC is the
+// double-float product of df_mac; the epilogue subtracts hi + lo from the
+// FP64 G and gathers the next block's rows / columns as the stripe kernel does.
+constexpr int kDfTile = 64, kDfLdA = 66;
+
+template <int K>
+__global__ void __launch_bounds__(256)
+    flush_df_tile_kernel(FlushArgs a, double *__restrict__ G, const float2 *__restrict__ A,
+                         const float2 *__restrict__ B, const int *__restrict__ accept_count,
+                         double *__restrict__ Gcol_next, double *__restrict__ Grow_next, int vec) {
+  extern __shared__ __align__(16) float2 dsm[];
+  float2 *As = dsm;                      // [K][kDfLdA]
+  float2 *Bs = dsm + K * kDfLdA;         // [K][kDfTile]
+  const int N = a.N, tid = threadIdx.x;
+  const int i0 = blockIdx.y * kDfTile, j0 = blockIdx.x * kDfTile;
+  const int ty = tid >> 4, tx = tid & 15;
+  const int m = accept_count ? *accept_count : a.kb;
+  const bool gather = a.nkb > 0 &&
+                      ((i0 < a.ns0 + a.nkb && i0 + kDfTile > a.ns0) || (j0 < a.ns0 + K && j0 + kDfTile > a.ns0));
+  if (m == 0 && !gather) return;
+  if (m > 0) {
+    for (int e = tid; e < kDfTile * K; e += 256) {
+      const int r = e / K, k = e % K;
+      const int i = i0 + r;
+      As[k * kDfLdA + r] = (i < N && k < m) ? A[(size_t)i * K + k] : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < kDfTile * K; e += 256) {
+      const int k = e / kDfTile, c = e % kDfTile;
+      const int j = j0 + c;
+      Bs[k * kDfTile + c] = (j < N && k < m) ? B[(size_t)k * N + j] : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sh[r][c] = sl[r][c] = 0.f;
+  for (int k = 0; k < m; ++k) {
+    const float4 a01 = *reinterpret_cast<const float4 *>(&As[k * kDfLdA + 4 * ty]);
+    const float4 a23 = *reinterpret_cast<const float4 *>(&As[k * kDfLdA + 4 * ty + 2]);
+    const float4 b01 = *reinterpret_cast<const float4 *>(&Bs[k * kDfTile + 4 * tx]);
+    const float4 b23 = *reinterpret_cast<const float4 *>(&Bs[k * kDfTile + 4 * tx + 2]);
+    const float ah[4] = {a01.x, a01.z, a23.x, a23.z}, al[4] = {a01.y, a01.w, a23.y, a23.w};
+    const float bh[4] = {b01.x, b01.z, b23.x, b23.z}, bl[4] = {b01.y, b01.w, b23.y, b23.w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) df_mac(ah[r], al[r], bh[c], bl[c], sh[r][c], sl[r][c]);
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + 4 * ty + r;
+    if (i >= N) continue;
+    const int jb = j0 + 4 * tx;
+    double v[4];
+    if (vec && jb + 3 < N) {
+      const double2 g0 = *reinterpret_cast<const double2 *>(&G[(size_t)i * N + jb]);
+      const double2 g1 = *reinterpret_cast<const double2 *>(&G[(size_t)i * N + jb + 2]);
+      v[0] = g0.x; v[1] = g0.y; v[2] = g1.x; v[3] = g1.y;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = (jb + c < N) ? G[(size_t)i * N + jb + c] : 0.0;
+    }
+    if (m > 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] -= f2d_bits(sh[r][c]) + f2d_bits(sl[r][c]);
+      if (vec && jb + 3 < N) {
+        *reinterpret_cast<double2 *>(&G[(size_t)i * N + jb]) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(&G[(size_t)i * N + jb + 2]) = make_double2(v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (jb + c < N) G[(size_t)i * N + jb + c] = v[c];
+      }
+    }
+    if (gather) {
+      const int it = i - a.ns0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = jb + c;
+        if (j >= N) continue;
+        const int jt = j - a.ns0;
+        if (it >= 0 && it < a.nkb) Grow_next[(size_t)it * N + j] = v[c];
+        if (jt >= 0 && jt < K) Gcol_next[(size_t)i * K + jt] = (jt < a.nkb) ? v[c] : 0.0;
+      }
+    }
+  }
+}
+
+template <int K>
+static cudaError_t launch_update_df_tiled(const FlushArgs &a, double *G, void *Abuf,
+                                          const double *Grow, const double *beta, const int *acc,
+                                          double *Gcol_next, double *Grow_next, cudaStream_t st) {
+  const float2 *A = static_cast<const float2 *>(Abuf);
+  float2 *B = static_cast<float2 *>(Abuf) + (size_t)a.N * K;
+  {
+    DQ_KSCOPE(KF_OTHER, st);
+    add_work(KF_OTHER, 2.0 * K * (double)a.N * a.kb, 8.0 * a.N * (double)(a.kb + K));
+    bmat_df_kernel<<<dim3((a.N + 255) / 256, K), 256, 0, st>>>(a, K, Grow, beta, acc, B);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int smem = (int)((size_t)K * (kDfLdA + kDfTile) * sizeof(float2));
+  cudaError_t e = ensure_smem_attr((const void *)flush_df_tile_kernel<K>, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((a.N + kDfTile - 1) / kDfTile, (a.N + kDfTile - 1) / kDfTile);
+  DQ_KSCOPE(KF_FLUSH, st);
+  add_work(KF_FLUSH, 2.0 * a.N * (double)a.N * a.kb,
+           (2.0 * a.N * (double)a.N + 2.0 * a.N * (double)a.kb) * sizeof(double));
+  // 16-byte vector access to G only where every row start is 16-byte aligned
+  const int vec = (a.N % 2 == 0) && ((reinterpret_cast<uintptr_t>(G) & 15) == 0);
+  flush_df_tile_kernel<K><<<grid, 256, smem, st>>>(a, G, A, B, acc, Gcol_next, Grow_next, vec);
+  return cudaGetLastError();
+}
+
+template <typename T, int K, bool DF>
+static cudaError_t launch_amat_K(const FlushArgs &a, const T *Gcol, const double *alpha,
+                                 const int *acc, void *Abuf, cudaStream_t st) {
+  const int rows_per = 256 / K;
+  DQ_KSCOPE(KF_OTHER, st);
+  add_work(KF_OTHER, 2.0 * a.N * (double)a.kb * a.kb, 8.0 * a.N * (double)(a.kb + K));
+  if constexpr (DF)
+    amat_kernel<T, float2><<<(a.N + rows_per - 1) / rows_per, 256, 0, st>>>(
+        a.N, K, a.kb, a.ldc, Gcol, alpha, a.lda, acc, static_cast<float2 *>(Abuf));
+  else
+    amat_kernel<T, T><<<(a.N + rows_per - 1) / rows_per, 256, 0, st>>>(
+        a.N, K, a.kb, a.ldc, Gcol, alpha, a.lda, acc, static_cast<T *>(Abuf));
+  return cudaGetLastError();
+}
+
+template <typename T, int K, bool DF>
+static cudaError_t launch_update_K(const FlushArgs &a, T *G, const void *Abuf, const T *Grow,
+                                   const double *beta, const int *acc, T *Gcol_next, T *Grow_next,
+                                   cudaStream_t st) {
   constexpr int SW = 4;
   const int grid = (a.N + SW - 1) / SW;
   DQ_KSCOPE(KF_FLUSH, st);
@@ -411,35 +520,117 @@ static cudaError_t launch_flush_K(const FlushArgs &a, T *G, const T *Gcol, const
   return cudaGetLastError();
 }
 
-template <typename T, bool DF>
-static cudaError_t launch_flush_any(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
-                                    const double *alpha, const double *beta, const int *acc,
-                                    void *Abuf, T *Gcol_next, T *Grow_next, cudaStream_t st) {
-  switch (K) {
-#define DQ_FLUSH_CASE(KK) \
-  case KK: return launch_flush_K<T, KK, DF>(a, G, Gcol, Grow, alpha, beta, acc, Abuf, Gcol_next, Grow_next, st);
-    DQ_FLUSH_CASE(4)
-    DQ_FLUSH_CASE(8)
-    DQ_FLUSH_CASE(16)
-    DQ_FLUSH_CASE(32)
-    DQ_FLUSH_CASE(64)
-#undef DQ_FLUSH_CASE
-    default: return cudaErrorInvalidValue;
+#define DQ_K_SWITCH(K, CALL) \
+  switch (K) {               \
+    case 4: { constexpr int KK = 4; return CALL; }   \
+    case 8: { constexpr int KK = 8; return CALL; }   \
+    case 16: { constexpr int KK = 16; return CALL; } \
+    case 32: { constexpr int KK = 32; return CALL; } \
+    case 64: { constexpr int KK = 64; return CALL; } \
+    default: return cudaErrorInvalidValue;           \
   }
+
+template <typename T>
+cudaError_t launch_amat(int K, const FlushArgs &a, const T *Gcol, const double *alpha,
+                        const int *acc, void *Abuf, bool df, cudaStream_t st) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (df) DQ_K_SWITCH(K, (launch_amat_K<double, KK, true>(a, Gcol, alpha, acc, Abuf, st)))
+  }
+  DQ_K_SWITCH(K, (launch_amat_K<T, KK, false>(a, Gcol, alpha, acc, Abuf, st)))
 }
+
+template <typename T>
+cudaError_t launch_flush_update(int K, const FlushArgs &a, T *G, const void *Abuf, const T *Grow,
+                                const double *beta, const int *acc, T *Gcol_next, T *Grow_next,
+                                bool df, cudaStream_t st) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (df)
+      DQ_K_SWITCH(K, (launch_update_df_tiled<KK>(a, G, const_cast<void *>(Abuf), Grow, beta, acc,
+                                                 Gcol_next, Grow_next, st)))
+  }
+  DQ_K_SWITCH(K, (launch_update_K<T, KK, false>(a, G, Abuf, Grow, beta, acc, Gcol_next, Grow_next,
+                                                st)))
+}
+#undef DQ_K_SWITCH
 
 template <typename T>
 cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
                          const double *alpha, const double *beta, const int *acc, void *Abuf,
                          T *Gcol_next, T *Grow_next, bool df, cudaStream_t st) {
-  if constexpr (std::is_same<T, double>::value) {
-    if (df)
-      return launch_flush_any<double, true>(K, a, G, Gcol, Grow, alpha, beta, acc, Abuf, Gcol_next,
-                                            Grow_next, st);
-  }
-  return launch_flush_any<T, false>(K, a, G, Gcol, Grow, alpha, beta, acc, Abuf, Gcol_next,
-                                    Grow_next, st);
+  cudaError_t e = launch_amat<T>(K, a, Gcol, alpha, acc, Abuf, df, st);
+  if (e != cudaSuccess) return e;
+  return launch_flush_update<T>(K, a, G, Abuf, Grow, beta, acc, Gcol_next, Grow_next, df, st);
 }
+
+// ----------------------------------------------------------------- look-ahead block
+// g' = G'[S', S'] of the next block S' = [ns0, ns0 + nkb) after the pending
+// flush of the current block, from the pre-flush G:
+//   g'[u][v] = G[i][j] - sum_m A[i][m] B[m][j],  i = ns0 + u, j = ns0 + v,
+//   B[m][j] = -sum_w beta[m][w] Grow[w][j]   (j is outside the current block),
+// the same entries the flush writes, in FP64. It lets the next block's
+// Metropolis run while the flush streams G. One CTA per column v.
+template <typename T, bool DFA>
+__global__ void __launch_bounds__(64)
+    lookahead_g_kernel(FlushArgs a, int K, const T *__restrict__ G, const void *__restrict__ A_,
+                       const T *__restrict__ Grow, const double *__restrict__ beta,
+                       const int *__restrict__ accept_count, double *__restrict__ gnext) {
+  __shared__ double bcol[64];
+  const int v = blockIdx.x, tid = threadIdx.x;
+  const int N = a.N, j = a.ns0 + v;
+  const int m = accept_count ? *accept_count : a.kb;
+  for (int mm = tid; mm < 64; mm += blockDim.x) {
+    double w = 0.0;
+    if (mm < m)
+      for (int u = 0; u < a.kb; ++u) w = fma(-beta[mm * a.ldb + u], (double)Grow[(size_t)u * N + j], w);
+    bcol[mm] = w;
+  }
+  __syncthreads();
+  for (int u = tid; u < a.nkb; u += blockDim.x) {
+    const int i = a.ns0 + u;
+    double val = (double)G[(size_t)i * N + j];
+    for (int mm = 0; mm < m; ++mm) {
+      double av;
+      if constexpr (DFA) {
+        const float2 p = static_cast<const float2 *>(A_)[(size_t)i * K + mm];
+        av = (double)p.x + (double)p.y;
+      } else {
+        av = (double)static_cast<const T *>(A_)[(size_t)i * K + mm];
+      }
+      val = fma(-av, bcol[mm], val);
+    }
+    gnext[u * a.nkb + v] = val;
+  }
+}
+
+template <typename T>
+cudaError_t launch_lookahead_g(int K, const FlushArgs &a, const T *G, const void *Abuf, bool df,
+                               const T *Grow, const double *beta, const int *acc, double *gnext,
+                               cudaStream_t st) {
+  if (a.nkb < 1 || a.nkb > 64 || K > 64) return cudaErrorInvalidValue;
+  DQ_KSCOPE(KF_OTHER, st);
+  add_work(KF_OTHER, 2.0 * a.nkb * (double)K * (a.kb + a.nkb), 8.0 * a.nkb * (double)(a.kb + a.nkb));
+  if (df && std::is_same<T, double>::value)
+    lookahead_g_kernel<T, true><<<a.nkb, 64, 0, st>>>(a, K, G, Abuf, Grow, beta, acc, gnext);
+  else
+    lookahead_g_kernel<T, false><<<a.nkb, 64, 0, st>>>(a, K, G, Abuf, Grow, beta, acc, gnext);
+  return cudaGetLastError();
+}
+template cudaError_t launch_lookahead_g<double>(int, const FlushArgs &, const double *, const void *,
+                                                bool, const double *, const double *, const int *,
+                                                double *, cudaStream_t);
+template cudaError_t launch_lookahead_g<float>(int, const FlushArgs &, const float *, const void *,
+                                               bool, const float *, const double *, const int *,
+                                               double *, cudaStream_t);
+template cudaError_t launch_amat<double>(int, const FlushArgs &, const double *, const double *,
+                                         const int *, void *, bool, cudaStream_t);
+template cudaError_t launch_amat<float>(int, const FlushArgs &, const float *, const double *,
+                                        const int *, void *, bool, cudaStream_t);
+template cudaError_t launch_flush_update<double>(int, const FlushArgs &, double *, const void *,
+                                                 const double *, const double *, const int *,
+                                                 double *, double *, bool, cudaStream_t);
+template cudaError_t launch_flush_update<float>(int, const FlushArgs &, float *, const void *,
+                                                const float *, const double *, const int *, float *,
+                                                float *, bool, cudaStream_t);
 template cudaError_t launch_flush<double>(int, const FlushArgs &, double *, const double *,
                                           const double *, const double *, const double *,
                                           const int *, void *, double *, double *, bool,

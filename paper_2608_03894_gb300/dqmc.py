@@ -123,6 +123,15 @@ class DQMC:
         f = np.ascontiguousarray(np.asarray(value, dtype=np.int8).reshape(self.M, self.N))
         check(self.lib.dqmc_set_field(self.h, f.ctypes.data_as(C.c_void_p)))
 
+    def replay(self, target, slice):
+        """Forced-flip up pass to `slice` towards the target field; returns the
+        fast path's running G(tau_slice) (FP64 N x N)."""
+        t = np.ascontiguousarray(np.asarray(target, dtype=np.int8).reshape(self.M, self.N))
+        G = np.empty((self.N, self.N), dtype=np.float64)
+        check(self.lib.dqmc_replay(self.h, t.ctypes.data_as(C.c_void_p), int(slice),
+                                   G.ctypes.data_as(C.c_void_p)))
+        return G
+
     def save(self, path):
         check(self.lib.dqmc_save(self.h, str(path).encode()))
 

@@ -24,10 +24,11 @@ def _need(t, dtype, name):
         raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
 
 
-def propagate(L, scale, side, X, Y=None, pre=None, post=None, vscale=None):
+def propagate(L, scale, side, X, Y=None, pre=None, post=None, vscale=None, df=False):
     """Eq. 5-6 kinetic propagator with fused diagonal scalings (see the header).
     side 0: Y = diag(post) e^{scale K} diag(pre) X diag(vscale), X is N x nvec;
-    side 1: Y = diag(vscale) X diag(pre) e^{scale K} diag(post), X is nvec x N."""
+    side 1: Y = diag(vscale) X diag(pre) e^{scale K} diag(post), X is nvec x N.
+    df: float64 data computed in double-float arithmetic."""
     import torch
     lib = _lib.load()
     dt = X.dtype
@@ -37,9 +38,12 @@ def propagate(L, scale, side, X, Y=None, pre=None, post=None, vscale=None):
         Y = torch.empty_like(X)
     nvec = X.shape[1] if side == 0 else X.shape[0]
     ld = X.shape[1]
-    fn = lib.dqmc_op_propagate_f64 if dt == torch.float64 else lib.dqmc_op_propagate_f32
     if dt not in (torch.float64, torch.float32):
         raise ValueError("float32 or float64 only")
+    if df and dt != torch.float64:
+        raise ValueError("double-float propagation takes float64 data")
+    fn = (lib.dqmc_op_propagate_df if df else lib.dqmc_op_propagate_f64) if dt == torch.float64 \
+        else lib.dqmc_op_propagate_f32
     check(fn(int(L), float(scale), int(side), _ptr(X), _ptr(Y), int(nvec), int(ld), _ptr(pre),
              _ptr(post), _ptr(vscale), _stream(torch)))
     return Y

@@ -84,6 +84,9 @@ def test_null_arguments(lib):
     assert lib.dqmc_sweep(h, -1, 0) == 1
     assert lib.dqmc_green(h, 0, None) == 1
     assert lib.dqmc_green(h, 999, C.c_void_p(1)) == 1   # slice out of range, checked first
+    assert lib.dqmc_replay(h, None, 1, C.c_void_p(1)) == 1
+    assert lib.dqmc_replay(h, C.c_void_p(1), 0, C.c_void_p(1)) == 1    # slice outside [1, M]
+    assert lib.dqmc_replay(h, C.c_void_p(1), 21, C.c_void_p(1)) == 1
     lib.dqmc_destroy(h)
 
 

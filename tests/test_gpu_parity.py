@@ -57,6 +57,28 @@ def test_propagate_f64_matches_dense_exponential(pkg, L, side):
     assert err < 1e-12 * max(1.0, np.max(np.abs(ref))), err
 
 
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 6, 8, 12, 16, 24, 36])
+@pytest.mark.parametrize("side", [0, 1])
+def test_propagate_double_float_matches_dense_exponential(pkg, L, side):
+    """FP64 data, double-float arithmetic (FP32 pairs, ~2^-47 per operation):
+    within 1e-13 of max |Y| after the log2(L^2) butterfly stages both ways."""
+    N = 3 * L * L
+    nvec = 37 if L > 2 else 5
+    scale = -0.1 if side == 0 else 0.1
+    X = random_matrix(N, nvec, seed=L) if side == 0 else random_matrix(nvec, N, seed=L)
+    rng = np.random.default_rng(200 + L)
+    pre, post = rng.uniform(0.5, 2.0, N), rng.uniform(0.5, 2.0, N)
+    vs = rng.uniform(0.5, 2.0, nvec)
+    E = olat.expm_hermitian(olat.kinetic_matrix(L), scale)
+    if side == 0:
+        ref = (post[:, None] * (E @ (pre[:, None] * X))) * vs[None, :]
+    else:
+        ref = vs[:, None] * (((X * pre[None, :]) @ E) * post[None, :])
+    Y = pkg.ops.propagate(L, scale, side, dev(X), pre=dev(pre), post=dev(post), vscale=dev(vs), df=True)
+    err = np.max(np.abs(Y.cpu().numpy() - ref))
+    assert err < 1e-13 * max(1.0, np.max(np.abs(ref))), err
+
+
 @pytest.mark.parametrize("L", [4, 12, 24, 36])
 def test_propagate_f32(pkg, L):
     N = 3 * L * L
@@ -216,6 +238,82 @@ def test_identical_field_history_20_sweeps(pkg, L, k, n_stab, beta, prec):
         assert np.max(np.abs(G - ref.G)) < 1e-10
         st = d.stats()
         assert st["accepted"] == ref.accepted and st["proposed"] == ref.proposed
+
+
+def _oracle_replay(par, n_stab, f0, f1, sl):
+    """The oracle's up pass to slice sl with the decisions forced towards f1:
+    wraps, one-at-a-time updates, refreshes at the checkpoints before sl."""
+    ch = odqmc.Chain(**par, seed=1, n_stab=n_stab, field=f0)
+    m = ch.model
+    c = 1
+    for l in range(1, sl + 1):
+        ch.G = m.B(ch.field[l - 1]) @ ch.G @ m.Binv(ch.field[l - 1])
+        ch.update_slice(l, 0, forced=(ch.field[l - 1] != f1[l - 1]))
+        if l == sl:
+            break
+        if l == ch.tau[c]:
+            ch.right[c] = ch._chunk_right(ch.right[c - 1].copy(), c)
+            ch._refresh(c)
+            c += 1
+    return ch
+
+
+@pytest.mark.parametrize("L,beta,k,n_stab,prec,sl,tol", [
+    (4, 2.0, 8, 10, "fp64", 13, 1e-10), (4, 2.0, 8, 10, "fp64", 20, 3e-9),
+    (12, 12.0, 32, 10, "fp64", 33, 1e-10), (12, 12.0, 32, 10, "fp64", 40, 3e-9),
+    (12, 12.0, 32, 10, "mixed", 33, 1e-9), (12, 12.0, 32, 10, "mixed", 40, 1e-8)])
+def test_replay_matches_oracle_green(pkg, L, beta, k, n_stab, prec, sl, tol):
+    """Forced flips of 10% of the sites of every slice (seeded), through the
+    fast path (wraps, delayed blocks, refreshes): the running G at the slice
+    equals the oracle's running G of the same replay, and both stay within the
+    drift bound 1e-8 of the from-scratch G of the field. Three slices after a
+    refresh the two agree to 1e-10 in FP64; at the end of a full interval each
+    has accumulated its own drift (the two stabilise differently: pre-pivoted
+    blocked QR here, column-pivoted QR in the oracle), hence 3e-9."""
+    par = dict(L=L, beta=beta, dtau=0.1, U=-4.0, mu=-1.0)
+    m = omodel.Model(**par)
+    f0 = random_field(m.M, m.N, seed=1)
+    flip = np.random.default_rng(2).random((m.M, m.N)) < 0.1
+    f1 = np.where(flip, -f0, f0).astype(np.int8)
+    with pkg.DQMC(**par, seed=1, k=k, n_stab=n_stab, precision=prec) as d:
+        d.field = f0
+        G = d.replay(f1, sl)
+        f = d.field
+        assert np.array_equal(f[:sl], f1[:sl]) and np.array_equal(f[sl:], f0[sl:])
+        ref = _oracle_replay(par, n_stab, f0, f1, sl)
+        assert np.array_equal(ref.field, f)
+        fresh = ogreen.green_udv(m, f, sl)
+        err, drift, drift_ref = (np.max(np.abs(G - ref.G)), np.max(np.abs(G - fresh)),
+                                 np.max(np.abs(ref.G - fresh)))
+        print(f"replay L={L} {prec} slice {sl}: |G-G_oracle| {err:.2e}, drift {drift:.2e}, "
+              f"oracle drift {drift_ref:.2e}")
+        assert err < tol
+        assert drift < 1e-8 and drift_ref < 1e-8
+        st = d.stats()
+        assert st["accepted"] == int(np.count_nonzero(f0[:sl] != f1[:sl]))
+        # the next sweep rebuilds the stacks from the new field (drift bar 1e-6)
+        d.sweep(1)
+        assert d.stats()["max_drift"] < 1e-6
+
+
+def test_replay_mixed_vs_fp64_full_size_L24(pkg):
+    """At the headline size (L = 24, N = 1728, M = 240, k = 32, n_stab = 8) the
+    oracle's from-scratch G is out of reach of a test; there the mixed fast
+    path is held to the FP64 fast path on the same replay (the FP64 path is
+    oracle-pinned at L <= 12), at the slice ending the longest refresh
+    interval, and to its own drift bound 1e-6."""
+    par = dict(L=24, beta=24.0, dtau=0.1, U=-4.0, mu=-1.0)
+    M, N = 240, 1728
+    f0 = random_field(M, N, seed=1)
+    flip = np.random.default_rng(2).random((M, N)) < 0.1
+    f1 = np.where(flip, -f0, f0).astype(np.int8)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        with pkg.DQMC(**par, seed=1, k=32, n_stab=8, precision=prec) as d:
+            d.field = f0
+            out[prec] = d.replay(f1, 16)
+            assert d.stats()["max_drift"] < 1e-6
+    assert np.max(np.abs(out["mixed"] - out["fp64"])) < 1e-6
 
 
 def test_measurements_equal_oracle_samples(pkg):
