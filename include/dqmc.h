@@ -251,6 +251,26 @@ dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *G
                               const float *Grow, const double *alpha, const double *beta,
                               const int *accept_count, void *stream);
 
+/* dqmc_op_flush_f64 without any device allocation. The paper has no
+ * counterpart: this is a deployment variant of the Sec. II delayed-update
+ * flush. Same arguments, semantics and FP64 result as dqmc_op_flush_f64, but
+ * the N x K scratch for the factor A (K = kb rounded up to a power of two >= 4)
+ * is a fixed device array compiled into the library: 248,832 doubles (1.9 MiB),
+ * enough for N <= 3888 (L = 36) at K = 64. Larger N * K -> DQMC_EINVAL, before
+ * any launch. For callers that cannot allocate device memory during the call:
+ * a process that has handed all device memory to its own pool or caching
+ * allocator up front (a cudaMallocAsync here could fail or grow a pool that
+ * must stay fixed), and host code that must not block on the device
+ * (cudaFree synchronises). The first call on a device resolves the array's
+ * device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture. Nothing has to start at zero: every
+ * scratch entry is written before it is read. The one array is shared by all
+ * calls on a device, so overlapping calls (several streams or host threads at
+ * once) race; serialise them. */
+dqmc_status dqmc_op_flush_f64_noalloc(int N, int site0, int kb, double *G, const double *Gcol,
+                                      const double *Grow, const double *alpha, const double *beta,
+                                      const int *accept_count, void *stream);
+
 /* FP64 GEMM of the stabilisation, C = alpha op(A) op(B) + beta C (row-major,
  * device), op = transpose when ta / tb. mode 0: FP64 FMA; 1: FP64-accurate
  * double-float product on the FP32 units; 2: FP64-accurate product from exact
