@@ -335,7 +335,11 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
   DQ_CHECK(ctx_alloc_n(c, &c->coef_b, 2 * (size_t)c->k * c->k));
   DQ_CHECK(ctx_alloc_n(c, &c->gnext, (size_t)c->k * c->k));
   if (!c->side) {
-    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    // highest priority: the serial Metropolis block is the critical path, its
+    // CTA should take the first SM that the concurrent flush frees
+    int prio_lo = 0, prio_hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    CK(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi));
     CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   }

@@ -319,15 +319,23 @@ __global__ void __launch_bounds__(256)
     // a CTA can only reuse this buffer parity after the next cluster barrier,
     // which every CTA reaches after its reads below
     cluster.sync();
+    {
+      // 256 / NB threads per column, each summing every (256 / NB)-th rank's
+      // partial: the remote loads are independent and overlap. The summation
+      // order is fixed, so every CTA gets bit-identical sums.
+      constexpr int NG = 256 / NB;
+      const int c = tid % NB, g = tid / NB;
+      double D = 0.0;
+      for (int r2 = g; r2 < ncta; r2 += NG) D += cluster.map_shared_rank(part, r2)[buf * NB + c];
+      red[g * NB + c] = D;
+      if (g == 0) sy0[c] = cluster.map_shared_rank(piv, owner)[buf * NB + c];
+    }
+    __syncthreads();
     if (tid < NB) {
       double D = 0.0;
-      for (int r2 = 0; r2 < ncta; ++r2) {
-        const double *rp = cluster.map_shared_rank(part, r2);
-        D += rp[buf * NB + tid];
-      }
-      const double *op = cluster.map_shared_rank(piv, owner);
+#pragma unroll
+      for (int g = 0; g < 256 / NB; ++g) D += red[g * NB + tid];
       sD[tid] = D;
-      sy0[tid] = op[buf * NB + tid];
     }
     __syncthreads();
     const double alpha = sy0[jj], sigma = sD[jj];
