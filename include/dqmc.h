@@ -103,26 +103,44 @@ typedef struct {
 dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, uint64_t seed,
                         dqmc_ctx **out);
 
-/* Options (numbers): "k" delay rank (4, 8, 16, 32 or 64; default 32), "n_stab"
- * slices between UDV refreshes (default 10), "precision" (0 = plain FP64;
- * 1 = mixed: FP64 data, ratios and recursions; propagation and flush in
- * double-float arithmetic (FP32 pairs) on the FP32 units, stabilisation
- * products as exact digit slices on the bf16 tensor cores; 2 = plain FP32
- * propagation and flush, which
- * drifts by 1e-3..1e-1 per refresh interval and exists for comparison),
- * "chain" (Philox chain id), "timing" (1 = per-phase CUDA-event timers,
- * 2 = also per kernel family; the events themselves cost time, so time
- * throughput with 0), "site_offsets" (1 = S_Pair phases use site positions
- * R + tau_a, 0 = cell positions), "bin" (measurements per bin, default 10),
- * "drift_limit" (hard limit, default 1e-3 -> DQMC_ENUMERIC), and, for the mixed
- * precision only: "df_flush" (default 1: the rank-m flush as double-float
- * products; 0 = native FP64), "df_prop" (default 1: the FFT propagation in
- * double-float arithmetic; 0 = native FP64), "stab_gemm" (stabilisation GEMMs: 0 = native
- * FP64, 1 = double-float, 2 = exact 7-bit digit slices on the bf16 tensor
- * cores, default 2), "gemm_sites" (32-bit mask of the stabilisation GEMM call
- * sites that use the stab_gemm variant, default all).
- * "k", "n_stab", "precision", "chain", "df_flush", "df_prop" and "stab_gemm" are accepted
- * only before the first sweep; later they return DQMC_ESTATE. */
+/* Options (numbers):
+ *   "k"          delay rank (4, 8, 16, 32 or 64; default 32);
+ *   "n_stab"     slices between UDV refreshes (default 10);
+ *   "precision"  0 = plain FP64 (default);
+ *                1 = mixed: FP64 data; propagation, flush and the Metropolis
+ *                    recursions in double-float arithmetic (FP32 pairs,
+ *                    ~2^-47) on the FP32 units; stabilisation products as
+ *                    exact digit slices on the bf16 tensor cores; Householder
+ *                    panels and triangular inverses in FP64;
+ *                2 = plain FP32 propagation and flush, which drifts by
+ *                    1e-3..1e-1 per refresh interval (for comparison);
+ *   "chain"      Philox chain id;
+ *   "timing"     1 = per-phase CUDA-event timers, 2 = also per kernel family
+ *                (the events cost time: time throughput with 0);
+ *   "site_offsets" 1 = S_Pair phases use site positions R + tau_a, 0 = cells;
+ *   "bin"        measurements per bin (default 10);
+ *   "drift_limit" hard limit on the refresh drift (default 1e-3 -> DQMC_ENUMERIC);
+ *   "metro_reserve" shared memory in bytes (0..232448, default 204800) that the
+ *                Metropolis block of the next delayed-update block claims while
+ *                it runs beside the current flush, so that it has an SM to
+ *                itself; 0 = only what it needs;
+ * mixed precision only (default 1; 0 = native FP64 for that step):
+ *   "df_flush"   rank-m flush as double-float products;
+ *   "df_prop"    FFT propagation in double-float arithmetic;
+ *   "df_metro"   Metropolis ratios and coefficient recursions in double-float
+ *                arithmetic (the decision u < R on the FP64 value of R);
+ *   "stab_gemm"  stabilisation GEMMs: 0 = FP64, 1 = double-float, 2 = exact
+ *                7-bit digit slices on the bf16 tensor cores (default 2);
+ *   "gemm_sites" 32-bit mask of the stabilisation GEMM call sites that use the
+ *                stab_gemm variant (default all);
+ *   "gemm_df_sites" with stab_gemm = 2: mask of those sites that use the
+ *                double-float GEMM instead (default 0). Site bits: 0 QR trailing
+ *                update, 1 explicit Q, 2 T update, 3 U_r^T U_l, 4 T_r T_l^T,
+ *                5 QR of the scale-separated matrix, 6 Q^T B, 7 triangular
+ *                solve, 8 final product.
+ * "k", "n_stab", "precision", "chain", "df_flush", "df_prop", "df_metro",
+ * "stab_gemm" and "gemm_df_sites" are accepted only before the first sweep;
+ * later they return DQMC_ESTATE. */
 dqmc_status dqmc_set_option(dqmc_ctx *ctx, const char *key, double value);
 
 /* Launch every kernel of this context on the given cudaStream_t (e.g. the

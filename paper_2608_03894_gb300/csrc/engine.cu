@@ -200,8 +200,11 @@ struct dqmc_ctx {
   void *Abuf = nullptr;                       // N x K rank-m factor A (or its FP32 pairs)
   int df_flush = 1;   // mixed: rank-m flush as double-float product (else FP64)
   int df_prop = 1;    // mixed: FFT propagation in double-float arithmetic (else FP64)
+  int df_metro = 1;   // mixed: Metropolis recursions in double-float arithmetic (else FP64)
+  int metro_reserve = 200 * 1024;  // shared memory the look-ahead Metropolis claims (own SM)
   int stab_gemm = 2;  // mixed: stabilisation GEMMs 0 FP64, 1 double-float, 2 tensor-core digit slices
   unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
+  unsigned gemm_df_sites = 0u;        // mixed: of those, the sites that use double-float products
   void *ozws = nullptr;  // digit-slice workspace
   size_t ozws_bytes = 0;
   int *ozexp = nullptr;
@@ -314,7 +317,7 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
   DQ_CHECK(ctx_alloc_n(c, &c->evi64, (size_t)N));
   DQ_CHECK(ctx_alloc_n(c, &c->ev32, (size_t)N));
   DQ_CHECK(ctx_alloc_n(c, &c->evi32, (size_t)N));
-  if (c->precision == 1 && c->stab_gemm == 1) {
+  if (c->precision == 1 && (c->stab_gemm == 1 || c->gemm_df_sites != 0)) {
     // split operands of the double-float GEMMs: at most M*K + K*N = 2 N^2 pairs
     c->dfws_elems = 2 * NN;
     DQ_CHECK(ctx_alloc_n(c, &c->dfws, c->dfws_elems));
@@ -499,6 +502,7 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
   T *Gc[2] = {static_cast<T *>(c->Gcol[0]), static_cast<T *>(c->Gcol[1])};
   T *Gr[2] = {static_cast<T *>(c->Grow[0]), static_cast<T *>(c->Grow[1])};
   const bool df = (c->precision == 1 && c->df_flush);
+  const bool dfm = (c->precision == 1 && c->df_metro);
   CK(launch_gather<T>(N, 0, std::min(K, N), K, G, Gc[0], Gr[0], c->stream));
   MetroArgs ma;
   ma.N = N;
@@ -516,7 +520,7 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
   ma.kb = std::min(K, N);
   ma.ld_g = N;
   CK(launch_metropolis(ma, Gr[0], sizeof(T) == 4, s, forced, c->coef_a, c->coef_b, c->acc,
-                       c->status, c->total_acc, c->stream));
+                       c->status, c->total_acc, c->stream, dfm));
   for (int b = 0; b < nblk; ++b) {
     const int s0 = b * K, kb = std::min(K, N - s0);
     const int par = b & 1;
@@ -532,7 +536,7 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
     fa.ldc = K;
     fa.ldb = K;
     fa.lda = K;
-    CK(launch_amat<T>(K, fa, Gc[par], al, acc, c->Abuf, df, c->stream));
+    CK(launch_amat<T>(K, fa, Gc[par], Gr[par], al, be, acc, c->Abuf, df, c->stream));
     if (fa.nkb > 0) {
       CK(launch_lookahead_g<T>(K, fa, G, c->Abuf, df, Gr[par], be, acc, c->gnext, c->stream));
       CK(cudaEventRecord(c->ev_fork, c->stream));
@@ -543,7 +547,7 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
       mn.ld_g = fa.nkb;
       CK(launch_metropolis(mn, c->gnext, false, s, forced ? forced + fa.ns0 : nullptr,
                            c->coef_a + (par ^ 1) * KK, c->coef_b + (par ^ 1) * KK, c->acc + (par ^ 1),
-                           c->status, c->total_acc, c->side));
+                           c->status, c->total_acc, c->side, dfm, c->metro_reserve));
       CK(cudaEventRecord(c->ev_join, c->side));
     }
     CK(launch_flush_update<T>(K, fa, G, c->Abuf, Gr[par], be, acc, Gc[par ^ 1], Gr[par ^ 1], df,
@@ -659,12 +663,18 @@ struct GemmModeScope {
     } else if (c->stab_gemm == 2 && c->ozws) {
       set_oz_workspace(c->ozws, c->ozws_bytes, c->ozexp, 2 * (size_t)c->N);
       set_gemm_oz(true);
+      if (c->gemm_df_sites && c->dfws) {
+        set_df_workspace(c->dfws, c->dfws_elems);
+        set_gemm_df(true);
+      }
     }
     set_gemm_site_mask(c->gemm_sites);
+    set_gemm_df_site_mask(c->stab_gemm == 2 ? c->gemm_df_sites : 0u);
   }
   ~GemmModeScope() {
     set_gemm_df(false);
     set_gemm_oz(false);
+    set_gemm_df_site_mask(0u);
   }
 };
 
@@ -934,12 +944,22 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) {
   } else if (k == "df_flush") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     c->df_flush = v != 0.0;
+  } else if (k == "metro_reserve") {
+    if (v < 0 || v > 227 * 1024) return fail(DQMC_EINVAL, "metro_reserve must be in [0, 232448] bytes");
+    c->metro_reserve = (int)v;
+  } else if (k == "df_metro") {
+    if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
+    c->df_metro = v != 0.0;
   } else if (k == "df_prop") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     c->df_prop = v != 0.0;
   } else if (k == "gemm_sites") {
     if (v < 0 || v > 4294967295.0) return fail(DQMC_EINVAL, "gemm_sites is a 32-bit mask");
     c->gemm_sites = (unsigned)v;
+  } else if (k == "gemm_df_sites") {
+    if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
+    if (v < 0 || v > 4294967295.0) return fail(DQMC_EINVAL, "gemm_df_sites is a 32-bit mask");
+    c->gemm_df_sites = (unsigned)v;
   } else if (k == "stab_gemm") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "stab_gemm must be 0, 1 or 2");

@@ -36,9 +36,13 @@ struct MetroArgs {
   uint32_t c2, c3;       // counter words 2 (2*sweep + pass) and 3 (chain | domain << 24)
   int slice0;            // counter word 1 (0-based slice)
 };
+// df: the recursions in double-float arithmetic (mixed precision), else FP64.
+// reserve_smem: shared memory to claim (bytes, <= 227 KB) so that the block
+// has its SM to itself while another kernel runs concurrently; 0 = its need.
 cudaError_t launch_metropolis(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
                               const uint8_t *forced, double *alpha, double *beta, int *accept_count,
-                              int *status, unsigned long long *total, cudaStream_t st);
+                              int *status, unsigned long long *total, cudaStream_t st,
+                              bool df = false, int reserve_smem = 0);
 
 struct FlushArgs {
   int N, s0, kb;   // current block
@@ -56,11 +60,13 @@ cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T
                          const double *alpha, const double *beta, const int *acc, void *Abuf,
                          T *Gcol_next, T *Grow_next, bool df, cudaStream_t st);
 
-// The two halves of launch_flush: A = Gcol alpha^T into Abuf, then the
-// rank-m update of G (with the next block's gather when a.nkb > 0).
+// The two halves of launch_flush: A = Gcol alpha^T into Abuf (and, when df,
+// the B factor after it), then the rank-m update of G (with the next block's
+// gather when a.nkb > 0).
 template <typename T>
-cudaError_t launch_amat(int K, const FlushArgs &a, const T *Gcol, const double *alpha,
-                        const int *acc, void *Abuf, bool df, cudaStream_t st);
+cudaError_t launch_amat(int K, const FlushArgs &a, const T *Gcol, const T *Grow,
+                        const double *alpha, const double *beta, const int *acc, void *Abuf,
+                        bool df, cudaStream_t st);
 template <typename T>
 cudaError_t launch_flush_update(int K, const FlushArgs &a, T *G, const void *Abuf, const T *Grow,
                                 const double *beta, const int *acc, T *Gcol_next, T *Grow_next,

@@ -124,8 +124,10 @@ static int grid_for(long work, int per = 256) {
 
 static thread_local int t_site = 0;
 static thread_local unsigned t_site_mask = 0xffffffffu;
+static thread_local unsigned t_df_site_mask = 0u;
 void set_gemm_site(int site) { t_site = site; }
 void set_gemm_site_mask(unsigned mask) { t_site_mask = mask; }
+void set_gemm_df_site_mask(unsigned mask) { t_df_site_mask = mask; }
 
 cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st) {
   DQ_KSCOPE(KF_OTHER, st);
@@ -138,6 +140,8 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
                   const double *cs, cudaStream_t st, int splitk) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const bool fast_site = (t_site_mask >> t_site) & 1u;
+  if (K > 0 && fast_site && ((t_df_site_mask >> t_site) & 1u) && gemm_df())
+    return dfgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, st, splitk, 304);
   if (K > 0 && fast_site && gemm_oz())
     return ozgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, st);
   if (K > 0 && fast_site && gemm_df())

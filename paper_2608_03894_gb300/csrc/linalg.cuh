@@ -51,6 +51,9 @@ enum GemmSite {
 };
 void set_gemm_site(int site);
 void set_gemm_site_mask(unsigned mask);
+// sites (within the site mask) that use the double-float GEMM even while the
+// digit-slice GEMM is on (needs a double-float workspace)
+void set_gemm_df_site_mask(unsigned mask);
 cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st);
 
 // Householder QR workspace for an n x n matrix: V (unit lower trapezoidal,

@@ -36,17 +36,28 @@ __device__ __forceinline__ int exp_field(double x) {
   return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
 }
 
-// Per-row (rows of op(A)) or per-column (columns of op(B)) maximum exponent
-// field. Elements are visited in storage order; `vec_of_row` says whether the
-// storage row index or the storage column index is the vector index.
-__global__ void oz_maxexp_kernel(const double *__restrict__ X, int rows, int cols, int ld,
-                                 int vec_is_row, int *__restrict__ emax) {
-  const long total = (long)rows * cols;
+// One operand of the slicing: the vectors are the rows of op(A) / the columns
+// of op(B); `vec_is_row` says whether the storage row index or the storage
+// column index is the vector index.
+struct OzOperand {
+  const double *X;
+  int rows, cols, ld, vec_is_row;
+  int *emax;             // per vector: maximum exponent field
+  int nvec, Kp;
+  unsigned short *out;   // digit planes [p][v][k]
+};
+
+// Maximum exponent field per vector, for both operands in one launch
+// (elements [0, rows_a cols_a) of A, then those of B), storage order.
+__global__ void oz_maxexp_kernel(OzOperand a, OzOperand b) {
+  const long na = (long)a.rows * a.cols, total = na + (long)b.rows * b.cols;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
-    const int r = (int)(e / cols), c = (int)(e % cols);
-    const int ex = exp_field(X[(size_t)r * ld + c]);
-    atomicMax(&emax[vec_is_row ? r : c], ex);
+    const OzOperand &o = e < na ? a : b;
+    const long f = e < na ? e : e - na;
+    const int r = (int)(f / o.cols), c = (int)(f % o.cols);
+    const int ex = exp_field(o.X[(size_t)r * o.ld + c]);
+    atomicMax(&o.emax[o.vec_is_row ? r : c], ex);
   }
 }
 
@@ -59,36 +70,36 @@ __device__ __forceinline__ unsigned short int_to_bf16_bits(int d) {
   return (unsigned short)(s | ((unsigned int)(msb + 127) << 7) | mant);
 }
 
-// Digits of element (v, k) of the vectors (rows of op(A) / columns of op(B)),
-// written to out[p][v][k] (bf16, row length Kp, zero padded); the vector's
-// exponent is emax[v]. Integer operations only.
-__global__ void oz_slice_kernel(const double *__restrict__ X, int rows, int cols, int ld,
-                                int vec_is_row, const int *__restrict__ emax, int nvec, int Kp,
-                                unsigned short *__restrict__ out) {
-  const long total = (long)nvec * Kp;
-  const size_t plane = (size_t)nvec * Kp;
+// Digits of element (v, k) of the vectors, written to out[p][v][k] (bf16, row
+// length Kp, zero padded); the vector's exponent is emax[v]. Both operands in
+// one launch (A's nvec_a Kp elements first). Integer operations only.
+__global__ void oz_slice_kernel(OzOperand a, OzOperand b) {
+  const long na = (long)a.nvec * a.Kp, total = na + (long)b.nvec * b.Kp;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
-    const int v = (int)(e / Kp), k = (int)(e % Kp);
+    const OzOperand &o = e < na ? a : b;
+    const long f = e < na ? e : e - na;
+    const size_t plane = (size_t)o.nvec * o.Kp;
+    const int v = (int)(f / o.Kp), k = (int)(f % o.Kp);
     double x = 0.0;
-    const int K = vec_is_row ? cols : rows;
-    if (k < K) x = vec_is_row ? X[(size_t)v * ld + k] : X[(size_t)k * ld + v];
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int ef = (int)((b >> 52) & 0x7ff);
+    const int K = o.vec_is_row ? o.cols : o.rows;
+    if (k < K) x = o.vec_is_row ? o.X[(size_t)v * o.ld + k] : o.X[(size_t)k * o.ld + v];
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7ff);
     unsigned long long F = 0;
     if (ef != 0 && ef != 0x7ff) {
-      const unsigned long long m53 = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
       // |x| / 2^{E} with E = emax - 1022 as a fixed-point number with 7 S = 63
       // fraction bits (m53 < 2^53, shift <= 10)
-      const int sh = ef - emax[v] + (7 * OZ_S - 53);
+      const int sh = ef - o.emax[v] + (7 * OZ_S - 53);
       F = sh >= 0 ? (m53 << sh) : (sh > -64 ? (m53 >> (-sh)) : 0ull);
     }
-    const int neg = (int)(b >> 63);
+    const int neg = (int)(bits >> 63);
 #pragma unroll
     for (int p = 1; p <= OZ_S; ++p) {
       int d = (int)((F >> (7 * OZ_S - 7 * p)) & 127ull);
       if (neg) d = -d;
-      out[(size_t)(p - 1) * plane + (size_t)v * Kp + k] = int_to_bf16_bits(d);
+      o.out[(size_t)(p - 1) * plane + (size_t)v * o.Kp + k] = int_to_bf16_bits(d);
     }
   }
 }
@@ -259,35 +270,17 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
   int *ea = t_ozexp, *eb = t_ozexp + M;
   cudaError_t e = cudaMemsetAsync(t_ozexp, 0, (size_t)(M + N) * sizeof(int), st);
   if (e != cudaSuccess) return e;
+  // op(A) rows: storage rows when !ta (M x K), storage columns when ta (K x M);
+  // op(B) columns: storage columns when !tb (K x N), storage rows when tb (N x K)
+  const OzOperand oa{A, ta ? K : M, ta ? M : K, lda, ta ? 0 : 1, ea, M, Kp, Ad};
+  const OzOperand ob{B, tb ? N : K, tb ? K : N, ldb, tb ? 1 : 0, eb, N, Kp, Bd};
   {
     DQ_KSCOPE(KF_OTHER, st);
-    // op(A) rows: storage rows when !ta; storage columns when ta
-    if (!ta)
-      oz_maxexp_kernel<<<oz_grid((long)M * K), 256, 0, st>>>(A, M, K, lda, 1, ea);
-    else
-      oz_maxexp_kernel<<<oz_grid((long)M * K), 256, 0, st>>>(A, K, M, lda, 0, ea);
+    oz_maxexp_kernel<<<oz_grid((long)M * K + (long)K * N), 256, 0, st>>>(oa, ob);
   }
   {
     DQ_KSCOPE(KF_OTHER, st);
-    // op(B) columns: storage columns when !tb; storage rows when tb
-    if (!tb)
-      oz_maxexp_kernel<<<oz_grid((long)K * N), 256, 0, st>>>(B, K, N, ldb, 0, eb);
-    else
-      oz_maxexp_kernel<<<oz_grid((long)K * N), 256, 0, st>>>(B, N, K, ldb, 1, eb);
-  }
-  {
-    DQ_KSCOPE(KF_OTHER, st);
-    if (!ta)
-      oz_slice_kernel<<<oz_grid((long)M * Kp), 256, 0, st>>>(A, M, K, lda, 1, ea, M, Kp, Ad);
-    else
-      oz_slice_kernel<<<oz_grid((long)M * Kp), 256, 0, st>>>(A, K, M, lda, 0, ea, M, Kp, Ad);
-  }
-  {
-    DQ_KSCOPE(KF_OTHER, st);
-    if (!tb)
-      oz_slice_kernel<<<oz_grid((long)N * Kp), 256, 0, st>>>(B, K, N, ldb, 0, eb, N, Kp, Bd);
-    else
-      oz_slice_kernel<<<oz_grid((long)N * Kp), 256, 0, st>>>(B, N, K, ldb, 1, eb, N, Kp, Bd);
+    oz_slice_kernel<<<oz_grid((long)(M + N) * Kp), 256, 0, st>>>(oa, ob);
   }
   const int smem = 2 * OZ_S * OZ_BM * OZ_LD * (int)sizeof(unsigned short);
   e = ensure_smem_attr((const void *)oz_gemm_kernel, smem);

@@ -18,6 +18,7 @@
 // Per block: metropolis (1 CTA, FP64), A = G[:,S] alpha (N x m, FP64), flush
 // (one CTA per 4-column stripe; B formed per stripe) whose epilogue gathers
 // G[:,S'] and G[S',:] of the next block.
+#include <algorithm>
 #include <type_traits>
 
 #include "df64.cuh"
@@ -62,40 +63,67 @@ template cudaError_t launch_gather<float>(int, int, int, int, const float *, flo
                                           cudaStream_t);
 
 // ----------------------------------------------------------------- Metropolis block
+// Arithmetic of the block's recursions: FP64, or double-float (df64, ~2^-47,
+// on the FP32 units) in mixed precision. The decision u < R compares the
+// FP64 value of R in both.
+template <typename T> struct MetroMath;
+template <> struct MetroMath<double> {
+  static __device__ __forceinline__ double from(double x) { return x; }
+  static __device__ __forceinline__ double to(double x) { return x; }
+  static __device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+};
+template <> struct MetroMath<df64> {
+  static __device__ __forceinline__ df64 from(double x) { return df_from(x); }
+  static __device__ __forceinline__ double to(df64 x) { return df_to(x); }
+  static __device__ __forceinline__ df64 mad(df64 a, df64 b, df64 c) { return a * b + c; }
+  // one FP32 quotient refined by one double-float residual step
+  static __device__ __forceinline__ df64 div(df64 a, df64 b) {
+    const float q1 = a.hi / b.hi;
+    const df64 r = a - b * df64(q1, 0.f);
+    const float q2 = r.hi / b.hi;
+    return fast_two_sum(q1, q2);
+  }
+};
+
 // One CTA of 4 warps. Lane u of every warp owns block sites u and u + 32.
 // On an accepted flip the four recursions of the accepted site run in
 // parallel, one per warp (warp 0: As, warp 1: Bs, warp 2: alpha, warp 3:
-// beta), each a length-m FP64 dot product per site; warp 0 keeps the current
+// beta), each a length-m dot product per site; warp 0 keeps the current
 // diagonal G~_uu in registers and takes the decisions.
 // Shared: g (kb x (kb+1)), As/Bs/al/be (K x kb each, row m = accepted flip m).
+template <typename T>
 __global__ void __launch_bounds__(128)
     metropolis_block_kernel(MetroArgs a, const void *__restrict__ g_, int g_is_f32, int8_t *s,
                             const uint8_t *__restrict__ forced, double *__restrict__ alpha_out,
                             double *__restrict__ beta_out, int *accept_count, int *status,
                             unsigned long long *total) {
-  extern __shared__ __align__(16) double sm[];
+  using MM = MetroMath<T>;
+  extern __shared__ __align__(16) unsigned char msm_raw[];
+  T *sm = reinterpret_cast<T *>(msm_raw);
   const int kb = a.kb;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ldg = kb + 1;
-  double *gs = sm;              // kb * ldg
-  double *As = gs + kb * ldg;   // [m][u]
-  double *Bs = As + kb * kb;
-  double *al = Bs + kb * kb;
-  double *be = al + kb * kb;
+  T *gs = sm;              // kb * ldg
+  T *As = gs + kb * ldg;   // [m][u]
+  T *Bs = As + kb * kb;
+  T *al = Bs + kb * kb;
+  T *be = al + kb * kb;
   // decision and coefficient of site j, double-buffered by the parity of j:
   // a rejected site has no second barrier, so the slot written at j + 2 must
   // differ from the one still being read at j
   __shared__ int s_dec[2];
-  __shared__ double s_coef[2];
+  __shared__ T s_coef[2];
 
   for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
     const int r = e / kb, c = e % kb;
     const size_t off = (size_t)r * a.ld_g + c;
-    gs[r * ldg + c] = g_is_f32 ? (double)static_cast<const float *>(g_)[off]
-                               : static_cast<const double *>(g_)[off];
+    gs[r * ldg + c] = MM::from(g_is_f32 ? (double)static_cast<const float *>(g_)[off]
+                                        : static_cast<const double *>(g_)[off]);
   }
   // warp 0: per-site state (sites lane and lane + 32)
-  double dtil[2] = {0.0, 0.0}, urand[2] = {0.0, 0.0};
+  T dtil[2] = {T(0), T(0)};
+  double urand[2] = {0.0, 0.0};
   int si[2] = {1, 1};
   if (warp == 0) {
 #pragma unroll
@@ -115,15 +143,17 @@ __global__ void __launch_bounds__(128)
     if (lane + 32 < kb) dtil[1] = gs[(lane + 32) * ldg + lane + 32];
   }
 
-  const double e2l = a.e2l, em2l = a.em2l;
+  const T e2l = MM::from(a.e2l), em2l = MM::from(a.em2l);
+  const T dpos = MM::from(a.em2l - 1.0), dneg = MM::from(a.e2l - 1.0);  // delta for s = +1 / -1
+  const T one = T(1), zero = T(0);
   int m = 0;
   for (int j = 0; j < kb; ++j) {
     if (warp == 0 && lane == (j & 31)) {
       const int h = j >> 5;
       // delta = e^{-2 lambda s} - 1, r = 1 + delta (1 - G~_jj), R = e^{2 lambda s} r^2
-      const double delta = (si[h] > 0 ? em2l : e2l) - 1.0;
-      const double r = 1.0 + delta * (1.0 - dtil[h]);
-      const double R = (si[h] > 0 ? e2l : em2l) * r * r;
+      const T delta = si[h] > 0 ? dpos : dneg;
+      const T r = one + delta * (one - dtil[h]);
+      const double R = MM::to((si[h] > 0 ? e2l : em2l) * r * r);
       int dec;
       if (!(R > 0.0) || !isfinite(R)) {
         dec = -1;
@@ -133,7 +163,7 @@ __global__ void __launch_bounds__(128)
         dec = (urand[h] < R) ? 1 : 0;
       }
       s_dec[j & 1] = dec;
-      s_coef[j & 1] = delta / r;
+      if (dec > 0) s_coef[j & 1] = MM::div(delta, r);
     }
     __syncthreads();
     const int dec = s_dec[j & 1];
@@ -142,27 +172,27 @@ __global__ void __launch_bounds__(128)
       break;
     }
     if (!dec) continue;
-    const double c = s_coef[j & 1];
+    const T c = s_coef[j & 1];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int u = lane + 32 * h;
       if (u >= kb) continue;
-      const double dj = (u == j) ? 1.0 : 0.0;
+      const T dj = (u == j) ? one : zero;
       if (warp == 0) {         // As_m[u] = c (g[u][j] - sum As_m'[u] Bs_m'[j])
-        double v = gs[u * ldg + j];
-        for (int mm = 0; mm < m; ++mm) v = fma(-As[mm * kb + u], Bs[mm * kb + j], v);
+        T v = gs[u * ldg + j];
+        for (int mm = 0; mm < m; ++mm) v = MM::mad(-As[mm * kb + u], Bs[mm * kb + j], v);
         As[m * kb + u] = c * v;
       } else if (warp == 1) {  // Bs_m[u] = delta_uj - (g[j][u] - sum As_m'[j] Bs_m'[u])
-        double v = gs[j * ldg + u];
-        for (int mm = 0; mm < m; ++mm) v = fma(-As[mm * kb + j], Bs[mm * kb + u], v);
+        T v = gs[j * ldg + u];
+        for (int mm = 0; mm < m; ++mm) v = MM::mad(-As[mm * kb + j], Bs[mm * kb + u], v);
         Bs[m * kb + u] = dj - v;
       } else if (warp == 2) {  // al_m[u] = c (delta_uj - sum al_m'[u] Bs_m'[j])
-        double v = dj;
-        for (int mm = 0; mm < m; ++mm) v = fma(-al[mm * kb + u], Bs[mm * kb + j], v);
+        T v = dj;
+        for (int mm = 0; mm < m; ++mm) v = MM::mad(-al[mm * kb + u], Bs[mm * kb + j], v);
         al[m * kb + u] = c * v;
       } else {                 // be_m[u] = delta_uj + sum As_m'[j] be_m'[u]
-        double v = dj;
-        for (int mm = 0; mm < m; ++mm) v = fma(As[mm * kb + j], be[mm * kb + u], v);
+        T v = dj;
+        for (int mm = 0; mm < m; ++mm) v = MM::mad(As[mm * kb + j], be[mm * kb + u], v);
         be[m * kb + u] = v;
       }
     }
@@ -171,7 +201,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int u = lane + 32 * h;
-        if (u < kb) dtil[h] -= As[m * kb + u] * Bs[m * kb + u];
+        if (u < kb) dtil[h] = MM::mad(-As[m * kb + u], Bs[m * kb + u], dtil[h]);
         if (u == j) {
           si[h] = -si[h];
           s[a.s0 + u] = (int8_t)si[h];
@@ -184,8 +214,8 @@ __global__ void __launch_bounds__(128)
   for (int e = threadIdx.x; e < a.K * a.K; e += blockDim.x) {
     const int r = e / a.K, u = e % a.K;
     const bool ok = (r < m && u < kb);
-    alpha_out[e] = ok ? al[r * kb + u] : 0.0;
-    beta_out[e] = ok ? be[r * kb + u] : 0.0;
+    alpha_out[e] = ok ? MM::to(al[r * kb + u]) : 0.0;
+    beta_out[e] = ok ? MM::to(be[r * kb + u]) : 0.0;
   }
   if (threadIdx.x == 0) {
     *accept_count = m;
@@ -195,15 +225,24 @@ __global__ void __launch_bounds__(128)
 
 cudaError_t launch_metropolis(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
                               const uint8_t *forced, double *alpha, double *beta, int *accept_count,
-                              int *status, unsigned long long *total, cudaStream_t st) {
+                              int *status, unsigned long long *total, cudaStream_t st, bool df,
+                              int reserve_smem) {
   if (a.kb < 1 || a.kb > 64 || a.kb > a.K) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)(a.kb * (a.kb + 1) + 4 * a.kb * a.kb) * sizeof(double);
-  cudaError_t e = ensure_smem_attr((const void *)metropolis_block_kernel,
-                                   (int)(5 * 64 * 65 * sizeof(double)));
+  // reserve_smem > the block's own need claims that much shared memory so
+  // that no CTA of a concurrently running kernel shares the SM
+  size_t smem = (size_t)(a.kb * (a.kb + 1) + 4 * a.kb * a.kb) * sizeof(double);
+  if ((size_t)reserve_smem > smem) smem = (size_t)reserve_smem;
+  const void *fn = df ? (const void *)metropolis_block_kernel<df64>
+                      : (const void *)metropolis_block_kernel<double>;
+  cudaError_t e = ensure_smem_attr(fn, (int)std::max<size_t>(smem, 5 * 64 * 65 * sizeof(double)));
   if (e != cudaSuccess) return e;
   DQ_KSCOPE(KF_METRO, st);
-  metropolis_block_kernel<<<1, 128, smem, st>>>(a, g, g_f32 ? 1 : 0, s, forced, alpha, beta,
-                                                accept_count, status, total);
+  if (df)
+    metropolis_block_kernel<df64><<<1, 128, smem, st>>>(a, g, g_f32 ? 1 : 0, s, forced, alpha, beta,
+                                                        accept_count, status, total);
+  else
+    metropolis_block_kernel<double><<<1, 128, smem, st>>>(a, g, g_f32 ? 1 : 0, s, forced, alpha,
+                                                          beta, accept_count, status, total);
   return cudaGetLastError();
 }
 
@@ -349,24 +388,43 @@ __global__ void __launch_bounds__(256)
 }
 
 // ----------------------------------------------------------------- tiled double-float flush
-// B[mm][j] = beta[mm][j - s0] [j in S] - sum_w beta[mm][w] Grow[w][j] for
-// mm < m (zero rows above), computed once per column in FP64 and stored as
-// (hi, lo) FP32 pairs, K x N row-major.
+// A (N x K pairs, as amat_kernel) and
+//   B[mm][j] = beta[mm][j - s0] [j in S] - sum_w beta[mm][w] Grow[w][j]
+// (K x N pairs, rows mm >= m zero) of the double-float flush in one launch,
+// both computed in FP64 and split into (hi, lo): blocks [0, nblk_a) form A,
+// the rest B (one column per thread, one mm per block row).
+template <int K>
 __global__ void __launch_bounds__(256)
-    bmat_df_kernel(FlushArgs a, int K, const double *__restrict__ Grow,
-                   const double *__restrict__ beta, const int *__restrict__ accept_count,
-                   float2 *__restrict__ B) {
-  const int N = a.N;
-  const int j = blockIdx.x * 256 + threadIdx.x, mm = blockIdx.y;
-  if (j >= N) return;
+    amat_bmat_df_kernel(FlushArgs a, const double *__restrict__ Gcol,
+                        const double *__restrict__ alpha, const double *__restrict__ Grow,
+                        const double *__restrict__ beta, const int *__restrict__ accept_count,
+                        float2 *__restrict__ A, float2 *__restrict__ B, int nblk_a) {
+  const int N = a.N, tid = threadIdx.x;
   const int m = accept_count ? *accept_count : a.kb;
-  double w = 0.0;
-  if (mm < m) {
-    const int js = j - a.s0;
-    if (js >= 0 && js < a.kb) w = beta[mm * a.ldb + js];
-    for (int u = 0; u < a.kb; ++u) w = fma(-beta[mm * a.ldb + u], Grow[(size_t)u * N + j], w);
+  if ((int)blockIdx.x < nblk_a) {
+    constexpr int rows_per = 256 / K;
+    const int i = blockIdx.x * rows_per + tid / K, mm = tid % K;
+    if (i >= N) return;
+    double v = 0.0;
+    if (mm < m) {
+      const double *gc = Gcol + (size_t)i * a.ldc;
+      const double *ar = alpha + (size_t)mm * a.lda;
+      for (int u = 0; u < a.kb; ++u) v = fma(gc[u], ar[u], v);
+    }
+    A[(size_t)i * K + mm] = split_df_bits(v);
+  } else {
+    const int nbj = (N + 255) / 256;
+    const int b = blockIdx.x - nblk_a, mm = b / nbj;
+    const int j = (b % nbj) * 256 + tid;
+    if (j >= N) return;
+    double w = 0.0;
+    if (mm < m) {
+      const int js = j - a.s0;
+      if (js >= 0 && js < a.kb) w = beta[mm * a.ldb + js];
+      for (int u = 0; u < a.kb; ++u) w = fma(-beta[mm * a.ldb + u], Grow[(size_t)u * N + j], w);
+    }
+    B[(size_t)mm * N + j] = split_df_bits(w);
   }
-  B[(size_t)mm * N + j] = split_df_bits(w);
 }
 
 // G[i0:i0+64, j0:j0+64] -= A B with A (N x K) and B (K x N) as FP32 pairs:
@@ -467,15 +525,11 @@ template <int K>
 static cudaError_t launch_update_df_tiled(const FlushArgs &a, double *G, void *Abuf,
                                           const double *Grow, const double *beta, const int *acc,
                                           double *Gcol_next, double *Grow_next, cudaStream_t st) {
+  // A and B (pairs) were formed by amat_bmat_df_kernel
   const float2 *A = static_cast<const float2 *>(Abuf);
-  float2 *B = static_cast<float2 *>(Abuf) + (size_t)a.N * K;
-  {
-    DQ_KSCOPE(KF_OTHER, st);
-    add_work(KF_OTHER, 2.0 * K * (double)a.N * a.kb, 8.0 * a.N * (double)(a.kb + K));
-    bmat_df_kernel<<<dim3((a.N + 255) / 256, K), 256, 0, st>>>(a, K, Grow, beta, acc, B);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  const float2 *B = static_cast<const float2 *>(Abuf) + (size_t)a.N * K;
+  (void)Grow;
+  (void)beta;
   const int smem = (int)((size_t)K * (kDfLdA + kDfTile) * sizeof(float2));
   cudaError_t e = ensure_smem_attr((const void *)flush_df_tile_kernel<K>, smem);
   if (e != cudaSuccess) return e;
@@ -490,15 +544,20 @@ static cudaError_t launch_update_df_tiled(const FlushArgs &a, double *G, void *A
 }
 
 template <typename T, int K, bool DF>
-static cudaError_t launch_amat_K(const FlushArgs &a, const T *Gcol, const double *alpha,
-                                 const int *acc, void *Abuf, cudaStream_t st) {
+static cudaError_t launch_amat_K(const FlushArgs &a, const T *Gcol, const T *Grow,
+                                 const double *alpha, const double *beta, const int *acc,
+                                 void *Abuf, cudaStream_t st) {
   const int rows_per = 256 / K;
   DQ_KSCOPE(KF_OTHER, st);
   add_work(KF_OTHER, 2.0 * a.N * (double)a.kb * a.kb, 8.0 * a.N * (double)(a.kb + K));
-  if constexpr (DF)
-    amat_kernel<T, float2><<<(a.N + rows_per - 1) / rows_per, 256, 0, st>>>(
-        a.N, K, a.kb, a.ldc, Gcol, alpha, a.lda, acc, static_cast<float2 *>(Abuf));
-  else
+  if constexpr (DF) {
+    // A and B of the double-float flush together
+    add_work(KF_OTHER, 2.0 * K * (double)a.N * a.kb, 8.0 * a.N * (double)(a.kb + K));
+    const int nblk_a = (a.N + rows_per - 1) / rows_per, nblk_b = ((a.N + 255) / 256) * K;
+    float2 *A = static_cast<float2 *>(Abuf);
+    amat_bmat_df_kernel<K><<<nblk_a + nblk_b, 256, 0, st>>>(a, Gcol, alpha, Grow, beta, acc, A,
+                                                            A + (size_t)a.N * K, nblk_a);
+  } else
     amat_kernel<T, T><<<(a.N + rows_per - 1) / rows_per, 256, 0, st>>>(
         a.N, K, a.kb, a.ldc, Gcol, alpha, a.lda, acc, static_cast<T *>(Abuf));
   return cudaGetLastError();
@@ -531,12 +590,14 @@ static cudaError_t launch_update_K(const FlushArgs &a, T *G, const void *Abuf, c
   }
 
 template <typename T>
-cudaError_t launch_amat(int K, const FlushArgs &a, const T *Gcol, const double *alpha,
-                        const int *acc, void *Abuf, bool df, cudaStream_t st) {
+cudaError_t launch_amat(int K, const FlushArgs &a, const T *Gcol, const T *Grow,
+                        const double *alpha, const double *beta, const int *acc, void *Abuf,
+                        bool df, cudaStream_t st) {
   if constexpr (std::is_same<T, double>::value) {
-    if (df) DQ_K_SWITCH(K, (launch_amat_K<double, KK, true>(a, Gcol, alpha, acc, Abuf, st)))
+    if (df)
+      DQ_K_SWITCH(K, (launch_amat_K<double, KK, true>(a, Gcol, Grow, alpha, beta, acc, Abuf, st)))
   }
-  DQ_K_SWITCH(K, (launch_amat_K<T, KK, false>(a, Gcol, alpha, acc, Abuf, st)))
+  DQ_K_SWITCH(K, (launch_amat_K<T, KK, false>(a, Gcol, Grow, alpha, beta, acc, Abuf, st)))
 }
 
 template <typename T>
@@ -557,7 +618,7 @@ template <typename T>
 cudaError_t launch_flush(int K, const FlushArgs &a, T *G, const T *Gcol, const T *Grow,
                          const double *alpha, const double *beta, const int *acc, void *Abuf,
                          T *Gcol_next, T *Grow_next, bool df, cudaStream_t st) {
-  cudaError_t e = launch_amat<T>(K, a, Gcol, alpha, acc, Abuf, df, st);
+  cudaError_t e = launch_amat<T>(K, a, Gcol, Grow, alpha, beta, acc, Abuf, df, st);
   if (e != cudaSuccess) return e;
   return launch_flush_update<T>(K, a, G, Abuf, Grow, beta, acc, Gcol_next, Grow_next, df, st);
 }
@@ -622,9 +683,11 @@ template cudaError_t launch_lookahead_g<float>(int, const FlushArgs &, const flo
                                                bool, const float *, const double *, const int *,
                                                double *, cudaStream_t);
 template cudaError_t launch_amat<double>(int, const FlushArgs &, const double *, const double *,
-                                         const int *, void *, bool, cudaStream_t);
-template cudaError_t launch_amat<float>(int, const FlushArgs &, const float *, const double *,
-                                        const int *, void *, bool, cudaStream_t);
+                                         const double *, const double *, const int *, void *, bool,
+                                         cudaStream_t);
+template cudaError_t launch_amat<float>(int, const FlushArgs &, const float *, const float *,
+                                        const double *, const double *, const int *, void *, bool,
+                                        cudaStream_t);
 template cudaError_t launch_flush_update<double>(int, const FlushArgs &, double *, const void *,
                                                  const double *, const double *, const int *,
                                                  double *, double *, bool, cudaStream_t);
