@@ -72,6 +72,8 @@ typedef struct {
 } dqmc_obs;
 
 /* Run statistics. */
+#define DQMC_KERNEL_FAMILIES 10
+
 typedef struct {
   long sweeps;           /* sweeps done since create/load */
   long proposed;         /* Metropolis proposals (2 N M per sweep) */
@@ -80,14 +82,17 @@ typedef struct {
   double last_drift;     /* same, over the last sweep only */
   double ms_wrap, ms_update, ms_stab, ms_measure; /* device time per phase (timing >= 1) */
   /* device time and launch count per kernel family (timing = 2): 0 FFT
-   * propagation, 1 Metropolis block, 2 rank-k flush, 3 GEMM, 4 QR panel,
-   * 5 measurement, 6 other */
-  double ms_kernel[7];
-  long n_kernel[7];
+   * propagation, 1 Metropolis block, 2 rank-k flush, 3 stabilisation GEMMs,
+   * 4 QR panels, 5 measurement, 6 other small kernels, 7 operand splitting of
+   * the emulated GEMMs, 8 delayed-update helpers (gathers, A/B factors,
+   * look-ahead block), 9 stabilisation helpers (T factors, triangular
+   * inverses, pivoting, scaling) */
+  double ms_kernel[DQMC_KERNEL_FAMILIES];
+  long n_kernel[DQMC_KERNEL_FAMILIES];
   /* algorithmic work per family (any timing): flops of the operation and
    * bytes of one read of its inputs plus one write of its outputs */
-  double flops_kernel[7];
-  double bytes_kernel[7];
+  double flops_kernel[DQMC_KERNEL_FAMILIES];
+  double bytes_kernel[DQMC_KERNEL_FAMILIES];
   unsigned long long launches; /* kernel launches issued for this context (any timing) */
 } dqmc_stats;
 

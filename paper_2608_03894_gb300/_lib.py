@@ -28,11 +28,12 @@ class Stats(C.Structure):
     _fields_ = [("sweeps", C.c_long), ("proposed", C.c_long), ("accepted", C.c_long),
                 ("max_drift", C.c_double), ("last_drift", C.c_double),
                 ("ms_wrap", C.c_double), ("ms_update", C.c_double), ("ms_stab", C.c_double),
-                ("ms_measure", C.c_double), ("ms_kernel", C.c_double * 7), ("n_kernel", C.c_long * 7),
-                ("flops_kernel", C.c_double * 7), ("bytes_kernel", C.c_double * 7),
+                ("ms_measure", C.c_double), ("ms_kernel", C.c_double * 10), ("n_kernel", C.c_long * 10),
+                ("flops_kernel", C.c_double * 10), ("bytes_kernel", C.c_double * 10),
                 ("launches", C.c_ulonglong)]
 
-KERNEL_FAMILIES = ("prop", "metropolis", "flush", "gemm", "qr_panel", "measure", "other")
+KERNEL_FAMILIES = ("prop", "metropolis", "flush", "gemm", "qr_panel", "measure", "other", "slice",
+                   "block_aux", "stab_aux")
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

@@ -79,7 +79,20 @@ constexpr uint32_t kDomainInit = 1u;
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 
 // Kernel families for per-family device timing (dqmc_stats.ms_kernel).
-enum KFam { KF_PROP = 0, KF_METRO, KF_FLUSH, KF_GEMM, KF_QRPANEL, KF_MEASURE, KF_OTHER, KF_COUNT };
+// kernel families for timing and work accounting (order = dqmc_stats arrays)
+enum KFam {
+  KF_PROP = 0,    // FFT propagation
+  KF_METRO,       // Metropolis block
+  KF_FLUSH,       // rank-m flush
+  KF_GEMM,        // stabilisation GEMMs
+  KF_QRPANEL,     // Householder panels
+  KF_MEASURE,     // measurements
+  KF_OTHER,       // remaining small kernels (exp(V), field init, drift)
+  KF_SLICE,       // operand splitting of the digit-slice / double-float GEMMs
+  KF_BLOCKAUX,    // delayed-update helpers: gathers, A/B factors, look-ahead block
+  KF_STABAUX,     // stabilisation helpers: T factors, triangular inverses, pivoting, scaling
+  KF_COUNT
+};
 
 // Optional per-launch event recorder, installed by the engine for the calling
 // thread while a context runs with per-kernel timing; every launch site wraps

@@ -152,14 +152,14 @@ cudaError_t dfgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
   if (na + nbn > t_ws_elems) return cudaErrorInvalidValue;
   float2 *As = t_ws, *Bs = t_ws + na;
   {
-    DQ_KSCOPE(KF_OTHER, st);
+    DQ_KSCOPE(KF_SLICE, st);
     if (!ta)
       split_df_kernel<<<grid_for_df((long)na), 256, 0, st>>>(A, M, K, lda, As);
     else
       split_df_kernel<<<grid_for_df((long)na), 256, 0, st>>>(A, K, M, lda, As);
   }
   {
-    DQ_KSCOPE(KF_OTHER, st);
+    DQ_KSCOPE(KF_SLICE, st);
     if (!tb)
       split_df_kernel<<<grid_for_df((long)nbn), 256, 0, st>>>(B, K, N, ldb, Bs);
     else

@@ -45,8 +45,8 @@ static thread_local KTimerSink *t_sink = nullptr;
 KTimerSink *&ktimer_sink() { return t_sink; }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
-static thread_local double t_flops[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
-static thread_local double t_bytes[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+static thread_local double t_flops[KF_COUNT] = {};
+static thread_local double t_bytes[KF_COUNT] = {};
 void add_work(int fam, double flops, double bytes) {
   t_flops[fam] += flops;
   t_bytes[fam] += bytes;
@@ -152,6 +152,8 @@ static dqmc_status get_table(int L, double scale, int prec, const void **out) {
 using namespace dq;
 
 // ---------------------------------------------------------------- context
+static_assert(KF_COUNT == DQMC_KERNEL_FAMILIES, "dqmc_stats arrays follow the kernel families");
+
 struct UDVd {
   double *U = nullptr, *D = nullptr, *T = nullptr;
 };
@@ -225,10 +227,10 @@ struct dqmc_ctx {
   double max_drift = 0.0, last_drift = 0.0;
   std::vector<std::array<double, 6>> samples;
   double ms_wrap = 0, ms_update = 0, ms_stab = 0, ms_measure = 0;
-  double ms_kernel[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
-  long n_kernel[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
-  double flops_kernel[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
-  double bytes_kernel[KF_COUNT] = {0, 0, 0, 0, 0, 0, 0};
+  double ms_kernel[KF_COUNT] = {};
+  long n_kernel[KF_COUNT] = {};
+  double flops_kernel[KF_COUNT] = {};
+  double bytes_kernel[KF_COUNT] = {};
   unsigned long long launches = 0;
 };
 
@@ -1322,6 +1324,7 @@ void dqmc_destroy(dqmc_ctx *c) {
     cudaEventDestroy(c->ev_fork);
     cudaEventDestroy(c->ev_join);
   }
+
   for (void *p : c->allocs) {
     if (c->ufree)
       c->ufree(p, c->uuser);

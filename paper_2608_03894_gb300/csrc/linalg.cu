@@ -130,7 +130,7 @@ void set_gemm_site_mask(unsigned mask) { t_site_mask = mask; }
 void set_gemm_df_site_mask(unsigned mask) { t_df_site_mask = mask; }
 
 cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
   return cudaGetLastError();
 }
@@ -146,8 +146,15 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
     return ozgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, st);
   if (K > 0 && fast_site && gemm_df())
     return dfgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, st, splitk, 304);
+  return dgemm_fp64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, st, splitk);
+}
+
+cudaError_t dgemm_fp64(bool ta, bool tb, int M, int N, int K, double alpha, const double *A,
+                       int lda, const double *B, int ldb, double beta, double *C, int ldc,
+                       const double *rs, const double *cs, cudaStream_t st, int splitk) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
   if (K <= 0) {
-    DQ_KSCOPE(KF_OTHER, st);
+    DQ_KSCOPE(KF_STABAUX, st);
     scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
     return cudaGetLastError();
   }
@@ -167,7 +174,7 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
   splitk = (K + klen - 1) / klen;
   const int atomic = splitk > 1;
   if (atomic) {
-    DQ_KSCOPE(KF_OTHER, st);
+    DQ_KSCOPE(KF_STABAUX, st);
     scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
   }
   dim3 grid((N + 63) / 64, (M + 63) / 64, splitk);
@@ -291,6 +298,7 @@ __global__ void __launch_bounds__(256)
   double *sy0 = sD + NB;                     // NB
   double *sw = sy0 + NB;                     // NB
   double *stau = sw + NB;                    // NB
+  __shared__ double ssc[3];                  // tau, beta, scal of the current reflector
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int e = tid; e < myrows * NB; e += 256) {
@@ -340,18 +348,25 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int g = 0; g < 256 / NB; ++g) D += red[g * NB + tid];
       sD[tid] = D;
+      if (tid == jj) {
+        // the reflector's scalars, once (FP64 sqrt and divisions are slow on this part)
+        const double alpha = sy0[jj], sigma = D;
+        double tau = 0.0, beta = alpha, scal = 0.0;
+        if (sigma > 0.0) {
+          const double nrm = sqrt(alpha * alpha + sigma);
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+        ssc[0] = tau;
+        ssc[1] = beta;
+        ssc[2] = scal;
+        stau[jj] = tau;
+      }
     }
     __syncthreads();
-    const double alpha = sy0[jj], sigma = sD[jj];
-    double tau = 0.0, beta = alpha, scal = 0.0;
-    if (sigma > 0.0) {
-      const double nrm = sqrt(alpha * alpha + sigma);
-      beta = (alpha >= 0.0) ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      scal = 1.0 / (alpha - beta);
-    }
+    const double tau = ssc[0], beta = ssc[1], scal = ssc[2];
     if (tid < NB) sw[tid] = (tid > jj && tid < nc) ? sy0[tid] + scal * sD[tid] : 0.0;
-    if (tid == 0) stau[jj] = tau;
     __syncthreads();
     for (int r = tid; r < myrows; r += 256) {
       const int lr = lr0 + r;
@@ -384,26 +399,69 @@ __global__ void __launch_bounds__(256)
 }
 
 // T (nc x nc, upper triangular, leading dimension NB) of the compact WY form
-// H_0 H_1 ... H_{nc-1} = I - V T V^T from the Gram matrix V^T V and tau:
-// T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V^T V)[0:j, j]. One CTA.
-__global__ void qr_t_kernel(const double *Gram, int ldg, const double *tau, int nc, int NB,
-                            double *T) {
-  extern __shared__ double st[];  // NB x NB
-  const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += blockDim.x) st[e] = 0.0;
-  __syncthreads();
-  for (int j = 0; j < nc; ++j) {
-    if (tid < j) {
-      double acc = 0.0;
-      for (int k = tid; k < j; ++k) acc = fma(st[tid * NB + k], Gram[(size_t)k * ldg + j], acc);
-      st[tid * NB + j] = -tau[j] * acc;
-    }
-    if (tid == j) st[j * NB + j] = tau[j];
-    __syncthreads();
+// H_0 H_1 ... H_{nc-1} = I - V T V^T. With every tau_j != 0,
+//     T^{-1} = diag(1/tau) + strictly-upper(V^T V)
+// (the product of two reflectors gives T = [[t0, -t0 t1 g], [0, t1]], whose
+// inverse is [[1/t0, g], [0, 1/t1]], g = v0^T v1; the same block argument
+// extends it to nc reflectors), so each column c of T is an independent back
+// substitution X[c][c] = tau_c, X[i][c] = -tau_i sum_{k>i} G[i][k] X[k][c]:
+// 16 warps, warp w takes columns w, 16 + w, nc - 1 - w and nc - 17 - w
+// (balanced lengths; a column two warps share is computed identically by
+// both), the dot products over k split over the lanes. If some tau_j = 0
+// (H_j = I) the serial recurrence T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j],
+// T_jj = tau_j is used instead. nc <= 64.
+__global__ void __launch_bounds__(512)
+    qr_t_kernel(const double *Gram, int ldg, const double *tau, int nc, int NB, double *T) {
+  __shared__ double g[64][64];
+  __shared__ double x[16][64];
+  __shared__ double st[64];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < 64 * 64; e += blockDim.x) {
+    const int i = e / 64, k = e % 64;
+    g[i][k] = (i < nc && k < nc) ? Gram[(size_t)i * ldg + k] : 0.0;
   }
-  for (int e = tid; e < NB * NB; e += blockDim.x) T[e] = st[e];
+  if (tid < 64) st[tid] = tid < nc ? tau[tid] : 0.0;
+  const int zero_tau = __syncthreads_or(tid < nc && tau[tid] == 0.0);
+  if (!zero_tau) {
+    const int cand[4] = {warp, 16 + warp, nc - 1 - warp, nc - 17 - warp};
+    for (int h = 0; h < 4; ++h) {
+      const int c = cand[h];
+      bool dup = c < 0 || c >= nc;
+      for (int h2 = 0; h2 < h; ++h2) dup = dup || cand[h2] == c;
+      if (dup) continue;
+      double *xs = x[warp];
+      for (int i = c; i >= 0; --i) {
+        double part = 0.0;
+        for (int k = i + 1 + lane; k <= c; k += 32) part = fma(g[i][k], xs[k], part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const double xi = (i == c) ? st[c] : -st[i] * part;
+        __syncwarp();
+        if (lane == 0) xs[i] = xi;
+        __syncwarp();
+      }
+      for (int i = lane; i < NB; i += 32) T[(size_t)i * NB + c] = i <= c ? xs[i] : 0.0;
+    }
+    for (int e = tid; e < NB * NB; e += blockDim.x)
+      if (e % NB >= nc) T[e] = 0.0;  // columns beyond the panel
+  } else if (warp == 0) {
+    // serial recurrence by one warp, T built in global memory (only this warp touches it)
+    for (int e = lane; e < NB * NB; e += 32) T[e] = 0.0;
+    __syncwarp();
+    for (int j = 0; j < nc; ++j) {
+      for (int i = lane; i < j; i += 32) {
+        double acc = 0.0;
+        for (int k = i; k < j; ++k) acc = fma(T[(size_t)i * NB + k], g[k][j], acc);
+        T[(size_t)i * NB + j] = -st[j] * acc;
+      }
+      if (lane == 0) T[(size_t)j * NB + j] = st[j];
+      __syncwarp();
+      __threadfence_block();
+    }
+  }
 }
 
+// Panel p (Householder column loop on one cluster), its Gram matrix V^T V and T.
 template <int NB>
 static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, cudaStream_t st) {
   const int ctas = w.ctas;
@@ -433,11 +491,11 @@ static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, c
   }
   // Gram = V_p^T V_p, then T_p
   const int m = n - p;
-  e = dgemm(true, false, nc, nc, m, 1.0, w.V + (size_t)p * n + p, n, w.V + (size_t)p * n + p, n, 0.0,
-            w.Gram, w.nb, nullptr, nullptr, st);
+  const double *Vp = w.V + (size_t)p * n + p;
+  e = dgemm(true, false, nc, nc, m, 1.0, Vp, n, Vp, n, 0.0, w.Gram, w.nb, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
-  DQ_KSCOPE(KF_OTHER, st);
-  qr_t_kernel<<<1, 64, (size_t)w.nb * w.nb * sizeof(double), st>>>(w.Gram, w.nb, w.tau + p, nc, w.nb,
+  DQ_KSCOPE(KF_STABAUX, st);
+  qr_t_kernel<<<1, 512, 0, st>>>(w.Gram, w.nb, w.tau + p, nc, w.nb,
                                                                    w.T + (size_t)(p / w.nb) * w.nb * w.nb);
   return cudaGetLastError();
 }
@@ -530,7 +588,7 @@ cudaError_t qr_solve_r(const double *A, int n, double *B, double *Z, int ncols, 
                        cudaStream_t st) {
   const int nb = w.nb;
   const int nblk = (n + nb - 1) / nb;
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   tri_inv_upper_blocks_kernel<<<nblk, 64, (size_t)nb * nb * sizeof(double), st>>>(A, n, nb, w.Rinv);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -562,7 +620,7 @@ __global__ void set_identity_kernel(double *A, int n, int ld) {
   }
 }
 cudaError_t set_identity(double *A, int n, int ld, cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   set_identity_kernel<<<grid_for((long)n * n), 256, 0, st>>>(A, n, ld);
   return cudaGetLastError();
 }
@@ -572,7 +630,7 @@ __global__ void set_value_kernel(double *x, long n, double v) {
     x[e] = v;
 }
 cudaError_t set_value(double *x, long n, double v, cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   set_value_kernel<<<grid_for(n), 256, 0, st>>>(x, n, v);
   return cudaGetLastError();
 }
@@ -595,7 +653,7 @@ __global__ void transpose_scale_kernel(const double *in, int ld, double *out, in
 cudaError_t transpose_scale(const double *in, int ld, double *out, int n, const double *rs,
                             cudaStream_t st) {
   dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   transpose_scale_kernel<<<grid, block, 0, st>>>(in, ld, out, n, rs);
   return cudaGetLastError();
 }
@@ -613,7 +671,7 @@ __global__ void scale_rows_cols_kernel(double *X, int n, int ld, const double *r
 }
 cudaError_t scale_rows_cols(double *X, int n, int ld, const double *rs, const double *cs,
                             cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   scale_rows_cols_kernel<<<grid_for((long)n * n), 256, 0, st>>>(X, n, ld, rs, cs);
   return cudaGetLastError();
 }
@@ -630,7 +688,7 @@ __global__ void column_norms_kernel(const double *X, int n, const double *D, dou
 }
 cudaError_t column_norms_scaled(const double *X, int n, const double *D, double *norms,
                                 cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   column_norms_kernel<<<(n + 127) / 128, 128, 0, st>>>(X, n, D, norms);
   return cudaGetLastError();
 }
@@ -679,7 +737,7 @@ cudaError_t argsort_desc(const double *key, int n, int *perm, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(argsort_desc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   argsort_desc_kernel<<<1, 1024, smem, st>>>(key, n, np, perm);
   return cudaGetLastError();
 }
@@ -697,7 +755,7 @@ __global__ void permute_udv_kernel(const double *X, const double *D, const doubl
 }
 cudaError_t permute_udv(const double *X, const double *D, const double *T, const int *perm, int n,
                         double *Xp, double *Dp, double *Tp, cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   permute_udv_kernel<<<grid_for((long)n * n), 256, 0, st>>>(X, D, T, perm, n, Xp, Dp, Tp);
   return cudaGetLastError();
 }
@@ -716,10 +774,10 @@ __global__ void udv_scale_kernel(double *R, int n, const double *Dp, const doubl
 }
 cudaError_t udv_diag_and_scale(double *R, int n, const double *Dp, double *Dnew, cudaStream_t st) {
   {
-    DQ_KSCOPE(KF_OTHER, st);
+    DQ_KSCOPE(KF_STABAUX, st);
     udv_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(R, n, Dp, Dnew);
   }
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   udv_scale_kernel<<<grid_for((long)n * n), 256, 0, st>>>(R, n, Dp, Dnew);
   return cudaGetLastError();
 }
@@ -746,14 +804,14 @@ __global__ void max_abs_diff_kernel(const double *A, const TB *B, long total, do
 cudaError_t max_abs_diff_f64(const double *A, const double *B, int n, double *out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   max_abs_diff_kernel<double><<<grid_for((long)n * n, 1024), 256, 0, st>>>(A, B, (long)n * n, out);
   return cudaGetLastError();
 }
 cudaError_t max_abs_diff_f32(const double *A, const float *B, int n, double *out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   max_abs_diff_kernel<float><<<grid_for((long)n * n, 1024), 256, 0, st>>>(A, B, (long)n * n, out);
   return cudaGetLastError();
 }
@@ -767,12 +825,12 @@ __global__ void f32_to_f64_kernel(const float *A, double *B, long n) {
     B[e] = (double)A[e];
 }
 cudaError_t convert_f64_to_f32(const double *A, float *B, long n, cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   f64_to_f32_kernel<<<grid_for(n), 256, 0, st>>>(A, B, n);
   return cudaGetLastError();
 }
 cudaError_t convert_f32_to_f64(const float *A, double *B, long n, cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   f32_to_f64_kernel<<<grid_for(n), 256, 0, st>>>(A, B, n);
   return cudaGetLastError();
 }
@@ -786,7 +844,7 @@ __global__ void split_scales_kernel(const double *D, int n, double *dmax_inv, do
   }
 }
 cudaError_t split_scales(const double *D, int n, double *dmax_inv, double *dmin, cudaStream_t st) {
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_STABAUX, st);
   split_scales_kernel<<<(n + 255) / 256, 256, 0, st>>>(D, n, dmax_inv, dmin);
   return cudaGetLastError();
 }

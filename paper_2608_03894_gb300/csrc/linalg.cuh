@@ -15,6 +15,10 @@ namespace dq {
 cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
                   const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
                   const double *cs, cudaStream_t st, int splitk = 0);
+// dgemm without the fast-variant dispatch: always FP64 FMA.
+cudaError_t dgemm_fp64(bool ta, bool tb, int M, int N, int K, double alpha, const double *A,
+                       int lda, const double *B, int ldb, double beta, double *C, int ldc,
+                       const double *rs, const double *cs, cudaStream_t st, int splitk = 0);
 cudaError_t dfgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
                    const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
                    const double *cs, cudaStream_t st, int splitk, int tiles_target);

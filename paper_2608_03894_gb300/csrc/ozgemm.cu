@@ -47,18 +47,57 @@ struct OzOperand {
   unsigned short *out;   // digit planes [p][v][k]
 };
 
-// Maximum exponent field per vector, for both operands in one launch
-// (elements [0, rows_a cols_a) of A, then those of B), storage order.
-__global__ void oz_maxexp_kernel(OzOperand a, OzOperand b) {
-  const long na = (long)a.rows * a.cols, total = na + (long)b.rows * b.cols;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const OzOperand &o = e < na ? a : b;
-    const long f = e < na ? e : e - na;
-    const int r = (int)(f / o.cols), c = (int)(f % o.cols);
-    const int ex = exp_field(o.X[(size_t)r * o.ld + c]);
-    atomicMax(&o.emax[o.vec_is_row ? r : c], ex);
+// Both slicing passes work on tiles of 32 vectors x 64 positions along K,
+// over both operands in one launch (A's tiles first). A tile is read in
+// storage order (rows of op(A) are contiguous when !ta, columns of op(B) are
+// strided when !tb: either way the reads are coalesced).
+constexpr int OZ_TV = 32, OZ_TK = 64;
+
+__device__ __forceinline__ int oz_tiles(const OzOperand &o) {
+  return ((o.nvec + OZ_TV - 1) / OZ_TV) * (o.Kp / OZ_TK);
+}
+
+// x of element (v, k) of the tile, in shared memory tile[v][k]
+__device__ __forceinline__ void oz_load_tile(const OzOperand &o, int v0, int k0, double (*tile)[OZ_TK + 1]) {
+  const int K = o.vec_is_row ? o.cols : o.rows;
+  for (int e = threadIdx.x; e < OZ_TV * OZ_TK; e += blockDim.x) {
+    int v, k;
+    if (o.vec_is_row) {
+      v = e / OZ_TK;
+      k = e % OZ_TK;
+    } else {
+      k = e / OZ_TV;
+      v = e % OZ_TV;
+    }
+    double x = 0.0;
+    if (v0 + v < o.nvec && k0 + k < K)
+      x = o.vec_is_row ? o.X[(size_t)(v0 + v) * o.ld + k0 + k] : o.X[(size_t)(k0 + k) * o.ld + v0 + v];
+    tile[v][k] = x;
   }
+}
+
+// Maximum exponent field per vector (emax must start at 0).
+__global__ void __launch_bounds__(256) oz_maxexp_kernel(OzOperand a, OzOperand b) {
+  __shared__ double tile[OZ_TV][OZ_TK + 1];
+  __shared__ int mx[OZ_TV];
+  const int ta = oz_tiles(a);
+  const bool isa = (int)blockIdx.x < ta;
+  const OzOperand &o = isa ? a : b;
+  const int t = isa ? blockIdx.x : blockIdx.x - ta;
+  const int ktiles = o.Kp / OZ_TK;
+  const int v0 = (t / ktiles) * OZ_TV, k0 = (t % ktiles) * OZ_TK;
+  if (threadIdx.x < OZ_TV) mx[threadIdx.x] = 0;
+  oz_load_tile(o, v0, k0, tile);
+  __syncthreads();
+  // 8 threads per vector, 8 positions each
+  const int v = threadIdx.x / 8, part = threadIdx.x % 8;
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < OZ_TK / 8; ++q) m = max(m, exp_field(tile[v][part * (OZ_TK / 8) + q]));
+  atomicMax(&mx[v], m);
+  __syncthreads();
+  if (threadIdx.x < OZ_TV && v0 + threadIdx.x < o.nvec && mx[threadIdx.x] > 0)
+    atomicMax(&o.emax[v0 + threadIdx.x], mx[threadIdx.x]);
 }
 
 __device__ __forceinline__ unsigned short int_to_bf16_bits(int d) {
@@ -71,19 +110,24 @@ __device__ __forceinline__ unsigned short int_to_bf16_bits(int d) {
 }
 
 // Digits of element (v, k) of the vectors, written to out[p][v][k] (bf16, row
-// length Kp, zero padded); the vector's exponent is emax[v]. Both operands in
-// one launch (A's nvec_a Kp elements first). Integer operations only.
-__global__ void oz_slice_kernel(OzOperand a, OzOperand b) {
-  const long na = (long)a.nvec * a.Kp, total = na + (long)b.nvec * b.Kp;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const OzOperand &o = e < na ? a : b;
-    const long f = e < na ? e : e - na;
-    const size_t plane = (size_t)o.nvec * o.Kp;
-    const int v = (int)(f / o.Kp), k = (int)(f % o.Kp);
-    double x = 0.0;
-    const int K = o.vec_is_row ? o.cols : o.rows;
-    if (k < K) x = o.vec_is_row ? o.X[(size_t)v * o.ld + k] : o.X[(size_t)k * o.ld + v];
+// length Kp, zero padded); the vector's exponent is emax[v]. Integer
+// operations only; the tile is staged in shared memory and the planes are
+// written along k (coalesced).
+__global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand a, OzOperand b) {
+  __shared__ double tile[OZ_TV][OZ_TK + 1];
+  const int ta = oz_tiles(a);
+  const bool isa = (int)blockIdx.x < ta;
+  const OzOperand &o = isa ? a : b;
+  const int t = isa ? blockIdx.x : blockIdx.x - ta;
+  const int ktiles = o.Kp / OZ_TK;
+  const int v0 = (t / ktiles) * OZ_TV, k0 = (t % ktiles) * OZ_TK;
+  oz_load_tile(o, v0, k0, tile);
+  __syncthreads();
+  const size_t plane = (size_t)o.nvec * o.Kp;
+  for (int e = threadIdx.x; e < OZ_TV * OZ_TK; e += blockDim.x) {
+    const int v = e / OZ_TK, k = e % OZ_TK;
+    if (v0 + v >= o.nvec) continue;
+    const double x = tile[v][k];
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const int ef = (int)((bits >> 52) & 0x7ff);
     unsigned long long F = 0;
@@ -91,15 +135,16 @@ __global__ void oz_slice_kernel(OzOperand a, OzOperand b) {
       const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
       // |x| / 2^{E} with E = emax - 1022 as a fixed-point number with 7 S = 63
       // fraction bits (m53 < 2^53, shift <= 10)
-      const int sh = ef - o.emax[v] + (7 * OZ_S - 53);
+      const int sh = ef - o.emax[v0 + v] + (7 * OZ_S - 53);
       F = sh >= 0 ? (m53 << sh) : (sh > -64 ? (m53 >> (-sh)) : 0ull);
     }
     const int neg = (int)(bits >> 63);
+    unsigned short *dst = o.out + (size_t)(v0 + v) * o.Kp + k0 + k;
 #pragma unroll
     for (int p = 1; p <= OZ_S; ++p) {
       int d = (int)((F >> (7 * OZ_S - 7 * p)) & 127ull);
       if (neg) d = -d;
-      o.out[(size_t)(p - 1) * plane + (size_t)v * o.Kp + k] = int_to_bf16_bits(d);
+      dst[(size_t)(p - 1) * plane] = int_to_bf16_bits(d);
     }
   }
 }
@@ -231,6 +276,125 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Register-blocked variant: per 16-wide k step a warp loads the fragments of
+// all 9 A planes once (36 registers) and, plane by plane, the B fragments of
+// its 4 n-tiles; every digit pair (p, q) with p + q <= 10 is then one MMA into
+// the accumulator of its level l = p + q (9 levels x 16 FP32 live). Shared
+// memory traffic per MMA drops from 0.75 to 0.15 ldmatrix, so the kernel is
+// bound by the MMA rate instead of shared-memory bandwidth. Same tiles,
+// staging, level folding and epilogue as oz_gemm_kernel.
+__global__ void __launch_bounds__(256)
+    oz_gemm_rb_kernel(int M, int N, int Kp, const unsigned short *__restrict__ Ad,
+                      const unsigned short *__restrict__ Bd, const int *__restrict__ ea,
+                      const int *__restrict__ eb, double alpha, double beta, double *__restrict__ C,
+                      int ldc, const double *__restrict__ rs, const double *__restrict__ cs,
+                      int kchunks, int atomic) {
+  extern __shared__ __align__(16) unsigned short osm[];
+  unsigned short *As = osm;                              // [p][64][OZ_LD]
+  unsigned short *Bs = osm + OZ_S * OZ_BM * OZ_LD;       // [q][64 (n)][OZ_LD]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;               // 4 x 2 warps
+  const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
+  const size_t aplane = (size_t)M * Kp, bplane = (size_t)N * Kp;
+
+  long long I[4][4];
+  float F[4][4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      I[t][r] = 0;
+      F[t][r] = 0.f;
+    }
+
+  const int kbeg = blockIdx.z * kchunks * OZ_KC;
+  const int kend = min(Kp, kbeg + kchunks * OZ_KC);
+  for (int k0 = kbeg; k0 < kend; k0 += OZ_KC) {
+    for (int e = tid; e < OZ_S * OZ_BM * (OZ_KC / 8); e += 256) {
+      const int p = e / (OZ_BM * (OZ_KC / 8));
+      const int rem = e % (OZ_BM * (OZ_KC / 8));
+      const int r = rem / (OZ_KC / 8), c8 = rem % (OZ_KC / 8);
+      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+      if (m0 + r < M) va = *reinterpret_cast<const uint4 *>(Ad + p * aplane + (size_t)(m0 + r) * Kp + k0 + c8 * 8);
+      if (n0 + r < N) vb = *reinterpret_cast<const uint4 *>(Bd + p * bplane + (size_t)(n0 + r) * Kp + k0 + c8 * 8);
+      *reinterpret_cast<uint4 *>(As + (p * OZ_BM + r) * OZ_LD + c8 * 8) = va;
+      *reinterpret_cast<uint4 *>(Bs + (p * OZ_BN + r) * OZ_LD + c8 * 8) = vb;
+    }
+    __syncthreads();
+    float acc[OZ_S][4][4];  // level l = p + q at index l - 2
+#pragma unroll
+    for (int l = 0; l < OZ_S; ++l)
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[l][t][r] = 0.f;
+#pragma unroll 1
+    for (int ks = 0; ks < OZ_KC; ks += 16) {
+      unsigned a[OZ_S][4];
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p)
+        ldmatrix_x4(a[p], As + ((p * OZ_BM) + wm * 16 + (lane & 15)) * OZ_LD + ks + (lane >> 4) * 8);
+#pragma unroll
+      for (int q = 0; q < OZ_S; ++q) {
+        unsigned b[2][4];
+#pragma unroll
+        for (int t2 = 0; t2 < 2; ++t2) {
+          const int nrow = t2 * 16 + ((lane >> 4) << 3) + (lane & 7);
+          const int kof = ((lane >> 3) & 1) * 8;
+          ldmatrix_x4(b[t2], Bs + ((q * OZ_BN) + wn * 32 + nrow) * OZ_LD + ks + kof);
+        }
+#pragma unroll
+        for (int p = 0; p + q <= OZ_S - 1; ++p) {  // digit indices p+1, q+1: level p + q + 2 <= OZ_S + 1
+#pragma unroll
+          for (int t2 = 0; t2 < 2; ++t2) {
+            mma_bf16(acc[p + q][2 * t2], a[p], b[t2][0], b[t2][1]);
+            mma_bf16(acc[p + q][2 * t2 + 1], a[p], b[t2][2], b[t2][3]);
+          }
+        }
+      }
+    }
+    // fold the exact level sums (level l = idx + 2): 2..7 into int64 with
+    // weight 2^{7(7-l)}, 8..10 into FP32 with weight 2^{-7(l-7)}
+#pragma unroll
+    for (int idx = 0; idx < OZ_S; ++idx) {
+      const int l = idx + 2;
+      if (l <= 7) {
+        const int shift = 7 * (7 - l);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) I[t][r] += ((long long)__float2int_rn(acc[idx][t][r])) << shift;
+      } else {
+        const float w = __int_as_float((127 - 7 * (l - 7)) << 23);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) F[t][r] = fmaf(acc[idx][t][r], w, F[t][r]);
+      }
+    }
+    __syncthreads();
+  }
+  const int g = lane >> 2, c2 = (lane & 3) * 2;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = m0 + wm * 16 + g + ((r >> 1) << 3);
+      const int j = n0 + wn * 32 + t * 8 + c2 + (r & 1);
+      if (i >= M || j >= N) continue;
+      const double dot = ((double)I[t][r] + (double)F[t][r]);
+      const int e2 = (ea[i] - 1022) + (eb[j] - 1022) - 49;
+      double v = ldexp(dot, e2) * alpha;
+      if (rs) v *= rs[i];
+      if (cs) v *= cs[j];
+      double *cp = C + (size_t)i * ldc + j;
+      if (atomic)
+        atomicAdd(cp, v);
+      else
+        *cp = (beta != 0.0) ? v + beta * (*cp) : v;
+    }
+}
+
 static thread_local unsigned short *t_ozws = nullptr;
 static thread_local size_t t_ozws_bytes = 0;
 static thread_local int *t_ozexp = nullptr;
@@ -252,12 +416,6 @@ size_t oz_workspace_bytes(int M, int N, int K) {
   return (size_t)OZ_S * ((size_t)M + N) * Kp * sizeof(unsigned short);
 }
 
-static int oz_grid(long work) {
-  long g = (work + 255) / 256;
-  if (g > 8192) g = 8192;
-  if (g < 1) g = 1;
-  return (int)g;
-}
 
 cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda,
                    const double *B, int ldb, double beta, double *C, int ldc, const double *rs,
@@ -274,16 +432,17 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
   // op(B) columns: storage columns when !tb (K x N), storage rows when tb (N x K)
   const OzOperand oa{A, ta ? K : M, ta ? M : K, lda, ta ? 0 : 1, ea, M, Kp, Ad};
   const OzOperand ob{B, tb ? N : K, tb ? K : N, ldb, tb ? 1 : 0, eb, N, Kp, Bd};
+  const int stiles = ((M + OZ_TV - 1) / OZ_TV + (N + OZ_TV - 1) / OZ_TV) * (Kp / OZ_TK);
   {
-    DQ_KSCOPE(KF_OTHER, st);
-    oz_maxexp_kernel<<<oz_grid((long)M * K + (long)K * N), 256, 0, st>>>(oa, ob);
+    DQ_KSCOPE(KF_SLICE, st);
+    oz_maxexp_kernel<<<stiles, 256, 0, st>>>(oa, ob);
   }
   {
-    DQ_KSCOPE(KF_OTHER, st);
-    oz_slice_kernel<<<oz_grid((long)(M + N) * Kp), 256, 0, st>>>(oa, ob);
+    DQ_KSCOPE(KF_SLICE, st);
+    oz_slice_kernel<<<stiles, 256, 0, st>>>(oa, ob);
   }
   const int smem = 2 * OZ_S * OZ_BM * OZ_LD * (int)sizeof(unsigned short);
-  e = ensure_smem_attr((const void *)oz_gemm_kernel, smem);
+  e = ensure_smem_attr((const void *)oz_gemm_rb_kernel, smem);
   if (e != cudaSuccess) return e;
   // one CTA per SM (shared memory); split K when the tiles do not fill the GPU
   const int tiles = ((N + OZ_BN - 1) / OZ_BN) * ((M + OZ_BM - 1) / OZ_BM);
@@ -306,7 +465,7 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
   DQ_KSCOPE(KF_GEMM, st);
   add_work(KF_GEMM, 2.0 * M * (double)N * K,
            8.0 * ((double)M * K + (double)K * N + (beta != 0.0 ? 2.0 : 1.0) * (double)M * N));
-  oz_gemm_kernel<<<grid, 256, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
+  oz_gemm_rb_kernel<<<grid, 256, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
                                           kchunks, atomic);
   return cudaGetLastError();
 }

@@ -53,7 +53,7 @@ cudaError_t launch_gather(int N, int s0, int kb, int K, const T *G, T *Gcol, T *
   int grid = (int)((work + 255) / 256);
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
-  DQ_KSCOPE(KF_OTHER, st);
+  DQ_KSCOPE(KF_BLOCKAUX, st);
   gather_block_kernel<T><<<grid, 256, 0, st>>>(N, s0, kb, K, G, Gcol, Grow);
   return cudaGetLastError();
 }
@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(256)
 // A (N x K pairs, as amat_kernel) and
 //   B[mm][j] = beta[mm][j - s0] [j in S] - sum_w beta[mm][w] Grow[w][j]
 // (K x N pairs, rows mm >= m zero) of the double-float flush in one launch,
-// both computed in FP64 and split into (hi, lo): blocks [0, nblk_a) form A,
-// the rest B (one column per thread, one mm per block row).
+// both accumulated in double-float arithmetic on the FP32 units: blocks
+// [0, nblk_a) form A, the rest B (one column per thread, one mm per block row).
 template <int K>
 __global__ void __launch_bounds__(256)
     amat_bmat_df_kernel(FlushArgs a, const double *__restrict__ Gcol,
@@ -405,25 +405,25 @@ __global__ void __launch_bounds__(256)
     constexpr int rows_per = 256 / K;
     const int i = blockIdx.x * rows_per + tid / K, mm = tid % K;
     if (i >= N) return;
-    double v = 0.0;
+    df64 v(0.f, 0.f);
     if (mm < m) {
       const double *gc = Gcol + (size_t)i * a.ldc;
       const double *ar = alpha + (size_t)mm * a.lda;
-      for (int u = 0; u < a.kb; ++u) v = fma(gc[u], ar[u], v);
+      for (int u = 0; u < a.kb; ++u) v = df_from(gc[u]) * df_from(ar[u]) + v;
     }
-    A[(size_t)i * K + mm] = split_df_bits(v);
+    A[(size_t)i * K + mm] = make_float2(v.hi, v.lo);
   } else {
     const int nbj = (N + 255) / 256;
     const int b = blockIdx.x - nblk_a, mm = b / nbj;
     const int j = (b % nbj) * 256 + tid;
     if (j >= N) return;
-    double w = 0.0;
+    df64 w(0.f, 0.f);
     if (mm < m) {
       const int js = j - a.s0;
-      if (js >= 0 && js < a.kb) w = beta[mm * a.ldb + js];
-      for (int u = 0; u < a.kb; ++u) w = fma(-beta[mm * a.ldb + u], Grow[(size_t)u * N + j], w);
+      if (js >= 0 && js < a.kb) w = df_from(beta[mm * a.ldb + js]);
+      for (int u = 0; u < a.kb; ++u) w = w - df_from(beta[mm * a.ldb + u]) * df_from(Grow[(size_t)u * N + j]);
     }
-    B[(size_t)mm * N + j] = split_df_bits(w);
+    B[(size_t)mm * N + j] = make_float2(w.hi, w.lo);
   }
 }
 
@@ -548,11 +548,11 @@ static cudaError_t launch_amat_K(const FlushArgs &a, const T *Gcol, const T *Gro
                                  const double *alpha, const double *beta, const int *acc,
                                  void *Abuf, cudaStream_t st) {
   const int rows_per = 256 / K;
-  DQ_KSCOPE(KF_OTHER, st);
-  add_work(KF_OTHER, 2.0 * a.N * (double)a.kb * a.kb, 8.0 * a.N * (double)(a.kb + K));
+  DQ_KSCOPE(KF_BLOCKAUX, st);
+  add_work(KF_BLOCKAUX, 2.0 * a.N * (double)a.kb * a.kb, 8.0 * a.N * (double)(a.kb + K));
   if constexpr (DF) {
     // A and B of the double-float flush together
-    add_work(KF_OTHER, 2.0 * K * (double)a.N * a.kb, 8.0 * a.N * (double)(a.kb + K));
+    add_work(KF_BLOCKAUX, 2.0 * K * (double)a.N * a.kb, 8.0 * a.N * (double)(a.kb + K));
     const int nblk_a = (a.N + rows_per - 1) / rows_per, nblk_b = ((a.N + 255) / 256) * K;
     float2 *A = static_cast<float2 *>(Abuf);
     amat_bmat_df_kernel<K><<<nblk_a + nblk_b, 256, 0, st>>>(a, Gcol, alpha, Grow, beta, acc, A,
@@ -668,8 +668,8 @@ cudaError_t launch_lookahead_g(int K, const FlushArgs &a, const T *G, const void
                                const T *Grow, const double *beta, const int *acc, double *gnext,
                                cudaStream_t st) {
   if (a.nkb < 1 || a.nkb > 64 || K > 64) return cudaErrorInvalidValue;
-  DQ_KSCOPE(KF_OTHER, st);
-  add_work(KF_OTHER, 2.0 * a.nkb * (double)K * (a.kb + a.nkb), 8.0 * a.nkb * (double)(a.kb + a.nkb));
+  DQ_KSCOPE(KF_BLOCKAUX, st);
+  add_work(KF_BLOCKAUX, 2.0 * a.nkb * (double)K * (a.kb + a.nkb), 8.0 * a.nkb * (double)(a.kb + a.nkb));
   if (df && std::is_same<T, double>::value)
     lookahead_g_kernel<T, true><<<a.nkb, 64, 0, st>>>(a, K, G, Abuf, Grow, beta, acc, gnext);
   else
