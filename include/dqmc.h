@@ -207,6 +207,21 @@ dqmc_status dqmc_replay(dqmc_ctx *ctx, const int8_t *target, int slice, double *
 dqmc_status dqmc_save(dqmc_ctx *ctx, const char *path);
 dqmc_status dqmc_load(dqmc_ctx *ctx, const char *path);
 
+/* Batched independent chains (Sec. III runs many independent Markov chains;
+ * here several of possibly different L on one GPU). dqmc_batch_create makes n
+ * contexts from params, n rows of (L, beta, dtau, U, mu, seed) doubles (L and
+ * seed integral), into the caller's array out[n]; chain i gets chain id i
+ * and its own non-blocking CUDA stream (destroyed with the context). Each
+ * context is then an ordinary one (options, measurements, fields, destroy).
+ * On any failure every context made so far is destroyed, out[] is NULL and
+ * the status of the failing chain is returned (DQMC_EINVAL for bad rows).
+ * dqmc_batch_sweep runs n_sweeps sweeps on the n distinct contexts at once,
+ * one host thread per chain, so that the kernels of different chains overlap
+ * on the GPU; it returns when all are done, with the first failing chain's
+ * status. */
+dqmc_status dqmc_batch_create(int n, const double *params, dqmc_ctx **out);
+dqmc_status dqmc_batch_sweep(dqmc_ctx **ctxs, int n, int n_sweeps, int measure);
+
 const char *dqmc_last_error(void);
 void dqmc_destroy(dqmc_ctx *ctx);
 

@@ -59,6 +59,8 @@ SIGNATURES = {
     "dqmc_save": (i32, [vp, C.c_char_p]),
     "dqmc_load": (i32, [vp, C.c_char_p]),
     "dqmc_destroy": (None, [vp]),
+    "dqmc_batch_create": (i32, [i32, vp, vp]),
+    "dqmc_batch_sweep": (i32, [vp, i32, i32, i32]),
     "dqmc_op_propagate_f64": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_propagate_f32": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_propagate_df": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),

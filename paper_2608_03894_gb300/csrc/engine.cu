@@ -20,6 +20,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -40,11 +41,13 @@ dqmc_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 // ---------------------------------------------------------------- launch accounting
-static std::atomic<unsigned long long> g_launches{0};
+// per host thread: a context is driven by one thread at a time, so the
+// difference of this counter around a call is that context's launches
+static thread_local unsigned long long t_launches = 0;
 static thread_local KTimerSink *t_sink = nullptr;
 KTimerSink *&ktimer_sink() { return t_sink; }
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void count_launch() { ++t_launches; }
+unsigned long long launch_count() { return t_launches; }
 static thread_local double t_flops[KF_COUNT] = {};
 static thread_local double t_bytes[KF_COUNT] = {};
 void add_work(int fam, double flops, double bytes) {
@@ -168,6 +171,7 @@ struct dqmc_ctx {
   double drift_limit = 1e-3;
   // runtime
   cudaStream_t stream = nullptr;
+  bool own_stream = false;  // created by dqmc_batch_create, destroyed with the context
   void *(*ualloc)(size_t, void *) = nullptr;
   void (*ufree)(void *, void *) = nullptr;
   void *uuser = nullptr;
@@ -1315,6 +1319,69 @@ dqmc_status dqmc_load(dqmc_ctx *c, const char *path) {
   return ensure_ready(c);
 }
 
+dqmc_status dqmc_batch_create(int n, const double *params, dqmc_ctx **out) {
+  if (n < 1 || !params || !out) return fail(DQMC_EINVAL, "need n >= 1, params and out");
+  for (int i = 0; i < n; ++i) out[i] = nullptr;
+  for (int i = 0; i < n; ++i) {
+    const double *p = params + 6 * (size_t)i;
+    if (p[0] != std::floor(p[0]) || !(p[5] >= 0.0) || p[5] != std::floor(p[5]) || p[5] > 9007199254740992.0)
+      return fail(DQMC_EINVAL, "chain " + std::to_string(i) + ": L and seed must be non-negative integers");
+  }
+  int dev = 0;
+  for (int i = 0; i < n; ++i) {
+    const double *p = params + 6 * (size_t)i;
+    dqmc_status st = dqmc_create((int)p[0], p[1], p[2], p[3], p[4], (uint64_t)p[5], &out[i]);
+    if (st == DQMC_OK) {
+      dqmc_ctx *c = out[i];
+      c->chain = i;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        c->stream = nullptr;
+        st = cuda_fail(e, "chain stream");
+      } else {
+        c->own_stream = true;
+        c->device = dev;
+      }
+    } else {
+      set_error("chain " + std::to_string(i) + ": " + g_last_error);
+    }
+    if (st != DQMC_OK) {
+      const std::string msg = g_last_error;
+      for (int j = 0; j <= i; ++j) {
+        dqmc_destroy(out[j]);
+        out[j] = nullptr;
+      }
+      set_error(msg);
+      return st;
+    }
+  }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_batch_sweep(dqmc_ctx **ctxs, int n, int n_sweeps, int measure) {
+  if (n < 1 || !ctxs) return fail(DQMC_EINVAL, "need n >= 1 and the contexts");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(DQMC_EINVAL, "context " + std::to_string(i) + " is NULL");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(DQMC_EINVAL, "a context appears twice");
+  }
+  std::vector<dqmc_status> rs(n, DQMC_OK);
+  std::vector<std::string> errs(n);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i] {
+      cudaSetDevice(ctxs[i]->device);
+      rs[i] = dqmc_sweep(ctxs[i], n_sweeps, measure);
+      if (rs[i] != DQMC_OK) errs[i] = g_last_error;
+    });
+  for (auto &t : th) t.join();
+  for (int i = 0; i < n; ++i)
+    if (rs[i] != DQMC_OK) return fail(rs[i], "chain " + std::to_string(i) + ": " + errs[i]);
+  return DQMC_OK;
+}
+
 void dqmc_destroy(dqmc_ctx *c) {
   if (!c) return;
   if (c->allocated || !c->allocs.empty()) cudaStreamSynchronize(c->stream);
@@ -1325,6 +1392,11 @@ void dqmc_destroy(dqmc_ctx *c) {
     cudaEventDestroy(c->ev_join);
   }
 
+  if (c->own_stream && c->stream) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+    c->stream = nullptr;
+  }
   for (void *p : c->allocs) {
     if (c->ufree)
       c->ufree(p, c->uuser);

@@ -9,6 +9,7 @@
 // trailing update is two GEMMs with the compact-WY factors V and
 // Y = V T^T (Q_panel = I - V T V^T).
 #include <cooperative_groups.h>
+#include <mutex>
 
 #include "linalg.cuh"
 #include "kernels.cuh"
@@ -207,7 +208,10 @@ static size_t qr_panel_smem_rows(int rows_per, int nb) {
 
 template <int NB> __global__ void qr_panel_kernel(double *, int, int, int, double *, double *);
 
+static std::mutex g_qr_mu;
+
 static int qr_cluster_ctas() {
+  std::lock_guard<std::mutex> lk(g_qr_mu);
   if (g_qr_ctas) return g_qr_ctas;
   int ctas = 8;
   const int want = 16;

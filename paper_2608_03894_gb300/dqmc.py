@@ -72,6 +72,17 @@ class DQMC:
                 check(self.lib.dqmc_set_allocator(self.h, self._alloc.alloc_cb, self._alloc.free_cb, None))
                 self.set_stream(torch.cuda.current_stream().cuda_stream)
 
+    @classmethod
+    def _from_handle(cls, h, L, beta, dtau):
+        self = cls.__new__(cls)
+        self.lib = _lib.load()
+        self.h = h
+        self.L = int(L)
+        self.N = 3 * self.L * self.L
+        self.M = int(round(beta / dtau))
+        self._alloc = None
+        return self
+
     # -- options / plumbing
     def set_option(self, key, value):
         check(self.lib.dqmc_set_option(self.h, key.encode(), float(value)))
@@ -148,6 +159,42 @@ class DQMC:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Independent chains of possibly different sizes on one GPU
+    (dqmc_batch_create / dqmc_batch_sweep): rows of params are
+    (L, beta, dtau, U, mu, seed); every chain has its own CUDA stream and
+    device memory from cudaMalloc. Options apply to every chain."""
+
+    def __init__(self, params, **options):
+        self.lib = _lib.load()
+        rows = [tuple(float(x) for x in r) for r in params]
+        n = len(rows)
+        flat = (C.c_double * (6 * n))(*[x for r in rows for x in r])
+        hs = (C.c_void_p * n)()
+        check(self.lib.dqmc_batch_create(n, flat, hs))
+        self._hs = hs
+        self.chains = [DQMC._from_handle(C.c_void_p(hs[i]), r[0], r[1], r[2]) for i, r in enumerate(rows)]
+        prec = {"fp64": 0, "mixed": 1, "fp32": 2}
+        for key, v in options.items():
+            v = prec.get(v, v) if key == "precision" else v
+            for c in self.chains:
+                c.set_option(key, v)
+
+    def sweep(self, n=1, measure=False):
+        check(self.lib.dqmc_batch_sweep(self._hs, len(self.chains), int(n), int(bool(measure))))
+
+    def close(self):
+        for c in self.chains:
+            c.close()
+        self.chains = []
 
     def __enter__(self):
         return self

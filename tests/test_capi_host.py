@@ -103,3 +103,15 @@ def test_operator_argument_validation(lib):
                                         None, p, p, p, p, None) == 1
     assert lib.dqmc_op_metropolis_block(48, 0, 8, p, 4, p, 0.5, 1, 0, 0, 1,
                                         None, p, p, p, p, None) == 1           # ld_g < kb
+
+
+def test_batch_create_validation(lib):
+    out = (C.c_void_p * 2)()
+    assert lib.dqmc_batch_create(0, None, out) == 1
+    bad_L = (C.c_double * 12)(4.5, 2.0, 0.1, -4.0, -1.0, 1.0, 4.0, 2.0, 0.1, -4.0, -1.0, 2.0)
+    assert lib.dqmc_batch_create(2, bad_L, out) == 1 and out[0] is None and out[1] is None
+    bad_seed = (C.c_double * 6)(4.0, 2.0, 0.1, -4.0, -1.0, -1.0)
+    assert lib.dqmc_batch_create(1, bad_seed, out) == 1
+    assert lib.dqmc_batch_sweep(None, 1, 1, 0) == 1
+    dup = (C.c_void_p * 2)(C.c_void_p(16), C.c_void_p(16))
+    assert lib.dqmc_batch_sweep(dup, 2, 1, 0) == 1          # the same context twice

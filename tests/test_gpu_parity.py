@@ -316,6 +316,21 @@ def test_replay_mixed_vs_fp64_full_size_L24(pkg):
     assert np.max(np.abs(out["mixed"] - out["fp64"])) < 1e-6
 
 
+def test_batched_chains_equal_single_chains(pkg):
+    """Chains of different sizes swept concurrently (own streams, one host
+    thread each) make exactly the decisions they make alone."""
+    params = [(4, 2.0, 0.1, -4.0, -1.0, 3), (6, 1.0, 0.1, -4.0, -1.0, 5), (4, 2.0, 0.1, -3.0, -1.0, 7)]
+    with pkg.Batch(params, k=8, n_stab=5, precision="mixed") as b:
+        b.sweep(3, measure=True)
+        fields = [c.field for c in b.chains]
+        nsamp = [c.measure()["n_samples"] for c in b.chains]
+    for i, (L, beta, dtau, U, mu, seed) in enumerate(params):
+        with pkg.DQMC(L, beta, dtau, U, mu, seed=seed, k=8, n_stab=5, precision="mixed", chain=i) as d:
+            d.sweep(3, measure=True)
+            assert np.array_equal(d.field, fields[i])
+            assert d.measure()["n_samples"] == nsamp[i]
+
+
 def test_measurements_equal_oracle_samples(pkg):
     par = dict(L=4, beta=1.0, dtau=0.1, U=-4.0, mu=-1.0)
     ref = odqmc.Chain(**par, seed=2, n_stab=5)
