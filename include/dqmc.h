@@ -112,11 +112,11 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *   "k"          delay rank (4, 8, 16, 32 or 64; default 32);
  *   "n_stab"     slices between UDV refreshes (default 10);
  *   "precision"  0 = plain FP64 (default);
- *                1 = mixed: FP64 data; propagation, flush and the Metropolis
- *                    recursions in double-float arithmetic (FP32 pairs,
- *                    ~2^-47) on the FP32 units; stabilisation products as
- *                    exact digit slices on the bf16 tensor cores; Householder
- *                    panels and triangular inverses in FP64;
+ *                1 = mixed: FP64 data; propagation and flush in
+ *                    double-float arithmetic (FP32 pairs, ~2^-47) on the
+ *                    FP32 units; stabilisation products as exact digit slices
+ *                    on the bf16 tensor cores; Metropolis, Householder panels
+ *                    and triangular inverses in FP64;
  *                2 = plain FP32 propagation and flush, which drifts by
  *                    1e-3..1e-1 per refresh interval (for comparison);
  *   "chain"      Philox chain id;
@@ -129,11 +129,13 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                Metropolis block of the next delayed-update block claims while
  *                it runs beside the current flush, so that it has an SM to
  *                itself; 0 = only what it needs;
- * mixed precision only (default 1; 0 = native FP64 for that step):
- *   "df_flush"   rank-m flush as double-float products;
- *   "df_prop"    FFT propagation in double-float arithmetic;
+ * mixed precision only (1 = double-float, 0 = native FP64 for that step):
+ *   "df_flush"   rank-m flush as double-float products (default 1);
+ *   "df_prop"    FFT propagation in double-float arithmetic (default 1);
  *   "df_metro"   Metropolis ratios and coefficient recursions in double-float
- *                arithmetic (the decision u < R on the FP64 value of R);
+ *                arithmetic, the decision u < R on the FP64 value of R
+ *                (default 0: no faster on the side stream, and its drift at
+ *                L = 36 is 1.7e-6 against 4.8e-7 in FP64);
  *   "stab_gemm"  stabilisation GEMMs: 0 = FP64, 1 = double-float, 2 = exact
  *                7-bit digit slices on the bf16 tensor cores (default 2);
  *   "gemm_sites" 32-bit mask of the stabilisation GEMM call sites that use the

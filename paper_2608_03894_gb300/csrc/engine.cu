@@ -206,7 +206,7 @@ struct dqmc_ctx {
   void *Abuf = nullptr;                       // N x K rank-m factor A (or its FP32 pairs)
   int df_flush = 1;   // mixed: rank-m flush as double-float product (else FP64)
   int df_prop = 1;    // mixed: FFT propagation in double-float arithmetic (else FP64)
-  int df_metro = 1;   // mixed: Metropolis recursions in double-float arithmetic (else FP64)
+  int df_metro = 0;   // mixed: Metropolis recursions in double-float arithmetic (else FP64)
   int metro_reserve = 200 * 1024;  // shared memory the look-ahead Metropolis claims (own SM)
   int stab_gemm = 2;  // mixed: stabilisation GEMMs 0 FP64, 1 double-float, 2 tensor-core digit slices
   unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
