@@ -165,124 +165,15 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
 
 // C = alpha diag(rs) (op(A) op(B)) diag(cs) + beta C from the digit planes.
 // CTA tile 64 x 64, 8 warps (warp tile 16 x 32 = 4 MMA n-tiles). Per K chunk
-// all 8 digit planes of the A and B tiles are staged in shared memory; the
-// level loop keeps one FP32 accumulator live.
-__global__ void __launch_bounds__(256)
-    oz_gemm_kernel(int M, int N, int Kp, const unsigned short *__restrict__ Ad,
-                   const unsigned short *__restrict__ Bd, const int *__restrict__ ea,
-                   const int *__restrict__ eb, double alpha, double beta, double *__restrict__ C,
-                   int ldc, const double *__restrict__ rs, const double *__restrict__ cs, int kchunks,
-                   int atomic) {
-  extern __shared__ __align__(16) unsigned short osm[];
-  unsigned short *As = osm;                              // [p][64][OZ_LD]
-  unsigned short *Bs = osm + OZ_S * OZ_BM * OZ_LD;       // [q][64 (n)][OZ_LD]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;               // 4 x 2 warps
-  const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
-  const size_t aplane = (size_t)M * Kp, bplane = (size_t)N * Kp;
-
-  long long I[4][4];
-  float F[4][4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      I[t][r] = 0;
-      F[t][r] = 0.f;
-    }
-
-  // split K: this CTA takes chunks [z * kchunks, (z + 1) * kchunks)
-  const int kbeg = blockIdx.z * kchunks * OZ_KC;
-  const int kend = min(Kp, kbeg + kchunks * OZ_KC);
-  for (int k0 = kbeg; k0 < kend; k0 += OZ_KC) {
-    // stage 8 planes of A (64 x 64) and B (64 x 64): 16-byte copies
-    for (int e = tid; e < OZ_S * OZ_BM * (OZ_KC / 8); e += 256) {
-      const int p = e / (OZ_BM * (OZ_KC / 8));
-      const int rem = e % (OZ_BM * (OZ_KC / 8));
-      const int r = rem / (OZ_KC / 8), c8 = rem % (OZ_KC / 8);
-      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-      if (m0 + r < M) va = *reinterpret_cast<const uint4 *>(Ad + p * aplane + (size_t)(m0 + r) * Kp + k0 + c8 * 8);
-      if (n0 + r < N) vb = *reinterpret_cast<const uint4 *>(Bd + p * bplane + (size_t)(n0 + r) * Kp + k0 + c8 * 8);
-      *reinterpret_cast<uint4 *>(As + (p * OZ_BM + r) * OZ_LD + c8 * 8) = va;
-      *reinterpret_cast<uint4 *>(Bs + (p * OZ_BN + r) * OZ_LD + c8 * 8) = vb;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int l = 2; l <= OZ_S + 1; ++l) {
-      float acc[4][4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[t][r] = 0.f;
-      const int plo = l - OZ_S > 1 ? l - OZ_S : 1, phi = l - 1 < OZ_S ? l - 1 : OZ_S;
-#pragma unroll 1
-      for (int p = plo; p <= phi; ++p) {
-        const int q = l - p;
-        const unsigned short *Ap = As + ((p - 1) * OZ_BM + wm * 16) * OZ_LD;
-        const unsigned short *Bq = Bs + ((q - 1) * OZ_BN + wn * 32) * OZ_LD;
-#pragma unroll
-        for (int ks = 0; ks < OZ_KC; ks += 16) {
-          unsigned a[4];
-          ldmatrix_x4(a, Ap + (lane & 15) * OZ_LD + ks + (lane >> 4) * 8);
-#pragma unroll
-          for (int t2 = 0; t2 < 2; ++t2) {  // two pairs of n-tiles
-            unsigned b[4];
-            const int nrow = t2 * 16 + ((lane >> 4) << 3) + (lane & 7);
-            const int kof = ((lane >> 3) & 1) * 8;
-            ldmatrix_x4(b, Bq + nrow * OZ_LD + ks + kof);
-            mma_bf16(acc[2 * t2], a, b[0], b[1]);
-            mma_bf16(acc[2 * t2 + 1], a, b[2], b[3]);
-          }
-        }
-      }
-      // fold the exact level sums: levels 2..7 into the int64 accumulator
-      // (weight 2^{7(7-l)}; per chunk < 2^55, over <= 256 chunks < 2^63),
-      // levels 8..10 into FP32 (their rounding is below 2^-58 of the result)
-      if (l <= 7) {
-        const int shift = 7 * (7 - l);
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) I[t][r] += ((long long)__float2int_rn(acc[t][r])) << shift;
-      } else {
-        const float w = __int_as_float((127 - 7 * (l - 7)) << 23);  // 2^{-7(l-7)}
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) F[t][r] = fmaf(acc[t][r], w, F[t][r]);
-      }
-    }
-    __syncthreads();
-  }
-  // epilogue: value = (I + F) 2^{-49} 2^{E_i + F_j}, E = emax - 1022
-  const int g = lane >> 2, c2 = (lane & 3) * 2;
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int i = m0 + wm * 16 + g + ((r >> 1) << 3);
-      const int j = n0 + wn * 32 + t * 8 + c2 + (r & 1);
-      if (i >= M || j >= N) continue;
-      const double dot = ((double)I[t][r] + (double)F[t][r]);
-      const int e2 = (ea[i] - 1022) + (eb[j] - 1022) - 49;
-      double v = ldexp(dot, e2) * alpha;
-      if (rs) v *= rs[i];
-      if (cs) v *= cs[j];
-      double *cp = C + (size_t)i * ldc + j;
-      if (atomic)
-        atomicAdd(cp, v);
-      else
-        *cp = (beta != 0.0) ? v + beta * (*cp) : v;
-    }
-}
-
-// Register-blocked variant: per 16-wide k step a warp loads the fragments of
-// all 9 A planes once (36 registers) and, plane by plane, the B fragments of
-// its 4 n-tiles; every digit pair (p, q) with p + q <= 10 is then one MMA into
-// the accumulator of its level l = p + q (9 levels x 16 FP32 live). Shared
-// memory traffic per MMA drops from 0.75 to 0.15 ldmatrix, so the kernel is
-// bound by the MMA rate instead of shared-memory bandwidth. Same tiles,
-// staging, level folding and epilogue as oz_gemm_kernel.
+// of 64 the 9 digit planes of the A and B tiles are staged in shared memory.
+// Register blocking: per 16-wide k step a warp loads the fragments of all 9 A
+// planes once (36 registers) and, plane by plane, the B fragments of its 4
+// n-tiles; every digit pair (p, q) with p + q <= 10 is one MMA into the
+// accumulator of its level l = p + q (9 levels x 16 FP32 live), 0.15
+// ldmatrix per MMA. After each chunk the exact level sums are folded: levels
+// 2..7 into an int64 accumulator (weight 2^{7(7-l)}), 8..10 into FP32; the
+// epilogue forms (I + F) 2^{-49} 2^{E_i + F_j} once per output (split K:
+// FP64 atomics).
 __global__ void __launch_bounds__(256)
     oz_gemm_rb_kernel(int M, int N, int Kp, const unsigned short *__restrict__ Ad,
                       const unsigned short *__restrict__ Bd, const int *__restrict__ ea,

@@ -15,9 +15,12 @@
 // Gamma = sum alpha beta^T never formed). The flush is a rank-m update with
 // m the number of accepted flips.
 //
-// Per block: metropolis (1 CTA, FP64), A = G[:,S] alpha (N x m, FP64), flush
-// (one CTA per 4-column stripe; B formed per stripe) whose epilogue gathers
-// G[:,S'] and G[S',:] of the next block.
+// Kernels: the Metropolis block (one CTA, FP64 or double-float recursions),
+// the A factor (and, for the double-float flush, the B factor), the
+// look-ahead G'[S',S'] of the next block from the pre-flush G (so that the
+// next block's decisions can run while this block's flush streams G), and the
+// flush itself -- FP64 / FP32 by column stripes, or double-float by 64 x 64
+// tiles -- whose epilogue gathers G[:,S'] and G[S',:] of the next block.
 #include <algorithm>
 #include <type_traits>
 
