@@ -136,7 +136,8 @@ def cpu_oracle_sample(w, budget_s=20.0):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     t1, n1, _ = odqmc.time_slice_visits(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], w["seed"], 1,
                                         n_stab=w["n_stab"], with_refresh=False)
-    visits = max(1, min(64, int(budget_s / max(t1, 1e-3))))
+    M = int(round(w["beta"] / w["dtau"]))
+    visits = max(1, min(64, M, int(budget_s / max(t1, 1e-3))))
     t, n, _ = odqmc.time_slice_visits(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], w["seed"], visits,
                                       n_stab=w["n_stab"], with_refresh=False)
     return {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -211,6 +212,22 @@ def run_micro(args):
     print(json.dumps({"micro": "prop", "results": out}), flush=True)
 
 
+def replica(w, rank):
+    """Replicas: every rank runs its own chain, seed + rank and chain id rank
+    (independent Philox streams), no collective on the data path."""
+    return {"seed": w["seed"] + rank, "chain": rank}
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's time (the whole-job time of weakly scaled replicas)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import ctypes as C
 
@@ -228,8 +245,9 @@ def run_ours(args, rank, world, local_rank):
     L, N = w["L"], 3 * w["L"] ** 2
     M = int(round(w["beta"] / w["dtau"]))
     units_per_step = 2 * N * M
-    d = pkg.DQMC(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], seed=w["seed"] + rank, k=w["k"],
-                 n_stab=w["n_stab"], precision=w["precision"], chain=rank)
+    rp = replica(w, rank)
+    d = pkg.DQMC(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], seed=rp["seed"], k=w["k"],
+                 n_stab=w["n_stab"], precision=w["precision"], chain=rp["chain"])
     stream = torch.cuda.current_stream()
     d.sweep(args.warmup)
     launches0 = d.stats()["launches"]
@@ -252,10 +270,7 @@ def run_ours(args, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1)
     st = d.stats()
     launches = st["launches"] - launches0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     value = units_per_step * args.steps * world / (ms / 1000.0)
     clocks = sampler.summary()
 
@@ -279,10 +294,7 @@ def run_ours(args, rank, world, local_rank):
             fin.copy_(fout)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(te, dist, "cuda")
         e2e = {"value": units_per_step * args.steps * world / te, "unit": UNIT,
                "h2d_bytes_per_step": M * N, "d2h_bytes_per_step": M * N + 6 * 8 * (-(-M // w["n_stab"]))}
 
