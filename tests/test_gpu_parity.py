@@ -331,6 +331,28 @@ def test_batched_chains_equal_single_chains(pkg):
             assert d.measure()["n_samples"] == nsamp[i]
 
 
+@pytest.mark.parametrize("L,beta,k,n_stab,prec", [
+    (1, 0.4, 4, 2, "fp64"),     # N = 3 (doubled bonds), one ragged block kb = 3 < K = 4
+    (2, 0.1, 4, 1, "fp64"),     # M = 1: a single slice, refresh after every visit
+    (3, 0.3, 8, 5, "fp64"),     # n_stab > M: one stack interval
+    (1, 0.4, 4, 2, "mixed"),
+    (3, 0.3, 8, 5, "mixed")])
+def test_degenerate_sizes_match_oracle(pkg, L, beta, k, n_stab, prec):
+    """Degenerate tori and intervals: identical decisions and G to the oracle."""
+    par = dict(L=L, beta=beta, dtau=0.1, U=-4.0, mu=-1.0)
+    ref = odqmc.Chain(**par, seed=2, n_stab=n_stab)
+    with pkg.DQMC(**par, seed=2, k=k, n_stab=n_stab, precision=prec) as d:
+        assert np.array_equal(d.field, ref.field)
+        for s in range(5):
+            d.sweep(1)
+            ref.sweep()
+            assert np.array_equal(d.field, ref.field), f"sweep {s}"
+        G, _ = d.running_green()
+        assert np.max(np.abs(G - ref.G)) < 1e-10
+        m = omodel.Model(**par)
+        assert np.max(np.abs(d.green(m.M) - ogreen.green_udv(m, d.field, m.M))) < 1e-10
+
+
 def test_measurements_equal_oracle_samples(pkg):
     par = dict(L=4, beta=1.0, dtau=0.1, U=-4.0, mu=-1.0)
     ref = odqmc.Chain(**par, seed=2, n_stab=5)
