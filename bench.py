@@ -199,11 +199,39 @@ def prop_microbench(L, prec, nstack, reps=5):
             "GB_s": round(nbytes / (ms * 1e-3) / 1e9, 1), "TFLOP_s": round(flops / (ms * 1e-3) / 1e12, 3)}
 
 
+def gemm_microbench(n, mode, reps=5):
+    """The stabilisation GEMM C = A B (n x n x n, FP64 data) in one of its
+    arithmetics: FP64 FMA, double-float, digit slices on the bf16 tensor cores."""
+    import torch
+
+    import paper_2608_03894_gb300 as pkg
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        pkg.ops.gemm(A, B, C, mode=mode)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        pkg.ops.gemm(A, B, C, mode=mode)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"n": n, "mode": mode, "ms": round(ms, 4), "TFLOP_s_fp64_equivalent": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 3)}
+
+
 def run_micro(args):
     import torch
     torch.cuda.set_device(0)
     peaks, src = load_peaks()
     out = []
+    if args.micro == "gemm":
+        for mode in args.micro_prec.split(","):
+            out.append(gemm_microbench(args.micro_n, mode))
+        print(json.dumps({"micro": "gemm", "results": out}), flush=True)
+        return
     for prec in args.micro_prec.split(","):
         r = prop_microbench(args.micro_L, prec, args.micro_stack)
         r["frac_of_hbm"] = round(r["GB_s"] / peaks["hbm_gbs"], 3)
@@ -400,8 +428,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--micro", default=None, choices=("prop",),
-                    help="only the FFT propagation microbenchmark (stacked operand larger than L2)")
+    ap.add_argument("--micro", default=None, choices=("prop", "gemm"),
+                    help="only a microbenchmark: the FFT propagation on a stacked operand larger "
+                         "than L2 (prop; --micro-prec fp32,df,fp64), or the stabilisation GEMM "
+                         "(gemm; --micro-prec f64,df,oz, size --micro-n)")
+    ap.add_argument("--micro-n", type=int, default=1728)
     ap.add_argument("--micro-L", type=int, default=24)
     ap.add_argument("--micro-stack", type=int, default=64)
     ap.add_argument("--micro-prec", default="fp32,df,fp64")
