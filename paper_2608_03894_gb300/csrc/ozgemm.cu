@@ -29,7 +29,6 @@ namespace dq {
 constexpr int OZ_S = 9;       // digits per value (63 bits)
 constexpr int OZ_KC = 64;      // K chunk
 constexpr int OZ_BM = 64, OZ_BN = 64;
-constexpr int OZ_LD = OZ_KC + 8;  // padded smem row (bf16): 144 B, conflict-free ldmatrix
 
 // exponent field (biased) of |x|; 0 for zero / subnormal
 __device__ __forceinline__ int exp_field(double x) {
@@ -164,25 +163,61 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
 }
 
 // C = alpha diag(rs) (op(A) op(B)) diag(cs) + beta C from the digit planes.
-// CTA tile 64 x 64, 8 warps (warp tile 16 x 32 = 4 MMA n-tiles). Per K chunk
-// of 64 the 9 digit planes of the A and B tiles are staged in shared memory.
-// Register blocking: per 16-wide k step a warp loads the fragments of all 9 A
-// planes once (36 registers) and, plane by plane, the B fragments of its 4
-// n-tiles; every digit pair (p, q) with p + q <= 10 is one MMA into the
-// accumulator of its level l = p + q (9 levels x 16 FP32 live), 0.15
-// ldmatrix per MMA. After each chunk the exact level sums are folded: levels
-// 2..7 into an int64 accumulator (weight 2^{7(7-l)}), 8..10 into FP32; the
-// epilogue forms (I + F) 2^{-49} 2^{E_i + F_j} once per output (split K:
-// FP64 atomics).
+// CTA tile 64 x 64, 8 warps (warp tile 16 x 32 = 4 MMA n-tiles). The 9 digit
+// planes of the A and B tiles are staged in shared memory 32 positions of K
+// at a time, double-buffered with cp.async: the next sub-chunk is in flight
+// while the MMAs of the current one run. Register blocking: per 16-wide k
+// step a warp loads the fragments of all 9 A planes once (36 registers) and,
+// plane by plane, the B fragments of its 4 n-tiles; every digit pair (p, q)
+// with p + q <= 10 is one MMA into the accumulator of its level l = p + q
+// (9 levels x 16 FP32 live), 0.15 ldmatrix per MMA. After every 64 positions
+// of K the exact level sums are folded: levels 2..7 into an int64
+// accumulator (weight 2^{7(7-l)}), 8..10 into FP32; the epilogue forms
+// (I + F) 2^{-49} 2^{E_i + F_j} once per output (split K: FP64 atomics).
+constexpr int OZ_SC = 32;           // staging sub-chunk of K
+constexpr int OZ_LDS = OZ_SC + 8;   // padded smem row (bf16): 80 B, conflict-free ldmatrix
+constexpr int OZ_BUF = OZ_S * (OZ_BM + OZ_BN) * OZ_LDS;  // one buffer, bf16 elements
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// Planes p of rows m0.. of A and n0.. of B, positions k0..k0+31, into buffer
+// sbuf ([A: p][64][OZ_LDS], then [B: q][64][OZ_LDS]); rows beyond M / N are
+// zero. Every global address is 16-byte aligned (Kp and k0 multiples of 32,
+// 8 bf16 per copy) and so is every shared one (80-byte rows).
+__device__ __forceinline__ void oz_stage(unsigned short *sbuf, const unsigned short *Ad,
+                                         const unsigned short *Bd, int M, int N, int Kp, int m0,
+                                         int n0, int k0, size_t aplane, size_t bplane) {
+  unsigned short *As = sbuf, *Bs = sbuf + OZ_S * OZ_BM * OZ_LDS;
+  for (int e = threadIdx.x; e < OZ_S * OZ_BM * (OZ_SC / 8); e += blockDim.x) {
+    const int p = e / (OZ_BM * (OZ_SC / 8));
+    const int rem = e % (OZ_BM * (OZ_SC / 8));
+    const int r = rem / (OZ_SC / 8), c8 = rem % (OZ_SC / 8);
+    unsigned short *da = As + (p * OZ_BM + r) * OZ_LDS + c8 * 8;
+    unsigned short *db = Bs + (p * OZ_BN + r) * OZ_LDS + c8 * 8;
+    if (m0 + r < M)
+      cp_async16(da, Ad + p * aplane + (size_t)(m0 + r) * Kp + k0 + c8 * 8);
+    else
+      *reinterpret_cast<uint4 *>(da) = make_uint4(0, 0, 0, 0);
+    if (n0 + r < N)
+      cp_async16(db, Bd + p * bplane + (size_t)(n0 + r) * Kp + k0 + c8 * 8);
+    else
+      *reinterpret_cast<uint4 *>(db) = make_uint4(0, 0, 0, 0);
+  }
+}
+
 __global__ void __launch_bounds__(256)
     oz_gemm_rb_kernel(int M, int N, int Kp, const unsigned short *__restrict__ Ad,
                       const unsigned short *__restrict__ Bd, const int *__restrict__ ea,
                       const int *__restrict__ eb, double alpha, double beta, double *__restrict__ C,
                       int ldc, const double *__restrict__ rs, const double *__restrict__ cs,
                       int kchunks, int atomic) {
-  extern __shared__ __align__(16) unsigned short osm[];
-  unsigned short *As = osm;                              // [p][64][OZ_LD]
-  unsigned short *Bs = osm + OZ_S * OZ_BM * OZ_LD;       // [q][64 (n)][OZ_LD]
+  extern __shared__ __align__(16) unsigned short osm[];  // two buffers of OZ_BUF
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 1, wn = warp & 1;               // 4 x 2 warps
   const int m0 = blockIdx.y * OZ_BM, n0 = blockIdx.x * OZ_BN;
@@ -197,34 +232,40 @@ __global__ void __launch_bounds__(256)
       I[t][r] = 0;
       F[t][r] = 0.f;
     }
+  float acc[OZ_S][4][4];  // level l = p + q at index l - 2
 
+  // split K: this CTA takes chunks [z * kchunks, (z + 1) * kchunks) of 64
   const int kbeg = blockIdx.z * kchunks * OZ_KC;
   const int kend = min(Kp, kbeg + kchunks * OZ_KC);
-  for (int k0 = kbeg; k0 < kend; k0 += OZ_KC) {
-    for (int e = tid; e < OZ_S * OZ_BM * (OZ_KC / 8); e += 256) {
-      const int p = e / (OZ_BM * (OZ_KC / 8));
-      const int rem = e % (OZ_BM * (OZ_KC / 8));
-      const int r = rem / (OZ_KC / 8), c8 = rem % (OZ_KC / 8);
-      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-      if (m0 + r < M) va = *reinterpret_cast<const uint4 *>(Ad + p * aplane + (size_t)(m0 + r) * Kp + k0 + c8 * 8);
-      if (n0 + r < N) vb = *reinterpret_cast<const uint4 *>(Bd + p * bplane + (size_t)(n0 + r) * Kp + k0 + c8 * 8);
-      *reinterpret_cast<uint4 *>(As + (p * OZ_BM + r) * OZ_LD + c8 * 8) = va;
-      *reinterpret_cast<uint4 *>(Bs + (p * OZ_BN + r) * OZ_LD + c8 * 8) = vb;
+  const int nsub = (kend - kbeg) / OZ_SC;  // even: Kp is a multiple of 64
+  if (nsub > 0) oz_stage(osm, Ad, Bd, M, N, Kp, m0, n0, kbeg, aplane, bplane);
+  cp_async_commit();
+  for (int it = 0; it < nsub; ++it) {
+    if (it + 1 < nsub) {
+      oz_stage(osm + ((it + 1) & 1) * OZ_BUF, Ad, Bd, M, N, Kp, m0, n0, kbeg + (it + 1) * OZ_SC,
+               aplane, bplane);
+      cp_async_commit();
+      cp_async_wait_one();
+    } else {
+      cp_async_wait_all();
     }
     __syncthreads();
-    float acc[OZ_S][4][4];  // level l = p + q at index l - 2
+    const unsigned short *As = osm + (it & 1) * OZ_BUF;
+    const unsigned short *Bs = As + OZ_S * OZ_BM * OZ_LDS;
+    if ((it & 1) == 0) {
 #pragma unroll
-    for (int l = 0; l < OZ_S; ++l)
+      for (int l = 0; l < OZ_S; ++l)
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
+        for (int t = 0; t < 4; ++t)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[l][t][r] = 0.f;
+          for (int r = 0; r < 4; ++r) acc[l][t][r] = 0.f;
+    }
 #pragma unroll 1
-    for (int ks = 0; ks < OZ_KC; ks += 16) {
+    for (int ks = 0; ks < OZ_SC; ks += 16) {
       unsigned a[OZ_S][4];
 #pragma unroll
       for (int p = 0; p < OZ_S; ++p)
-        ldmatrix_x4(a[p], As + ((p * OZ_BM) + wm * 16 + (lane & 15)) * OZ_LD + ks + (lane >> 4) * 8);
+        ldmatrix_x4(a[p], As + ((p * OZ_BM) + wm * 16 + (lane & 15)) * OZ_LDS + ks + (lane >> 4) * 8);
 #pragma unroll
       for (int q = 0; q < OZ_S; ++q) {
         unsigned b[2][4];
@@ -232,7 +273,7 @@ __global__ void __launch_bounds__(256)
         for (int t2 = 0; t2 < 2; ++t2) {
           const int nrow = t2 * 16 + ((lane >> 4) << 3) + (lane & 7);
           const int kof = ((lane >> 3) & 1) * 8;
-          ldmatrix_x4(b[t2], Bs + ((q * OZ_BN) + wn * 32 + nrow) * OZ_LD + ks + kof);
+          ldmatrix_x4(b[t2], Bs + ((q * OZ_BN) + wn * 32 + nrow) * OZ_LDS + ks + kof);
         }
 #pragma unroll
         for (int p = 0; p + q <= OZ_S - 1; ++p) {  // digit indices p+1, q+1: level p + q + 2 <= OZ_S + 1
@@ -244,25 +285,28 @@ __global__ void __launch_bounds__(256)
         }
       }
     }
-    // fold the exact level sums (level l = idx + 2): 2..7 into int64 with
-    // weight 2^{7(7-l)}, 8..10 into FP32 with weight 2^{-7(l-7)}
+    if (it & 1) {
+      // fold the exact level sums of 64 positions (level l = idx + 2): 2..7 into
+      // int64 with weight 2^{7(7-l)}, 8..10 into FP32 with weight 2^{-7(l-7)}
 #pragma unroll
-    for (int idx = 0; idx < OZ_S; ++idx) {
-      const int l = idx + 2;
-      if (l <= 7) {
-        const int shift = 7 * (7 - l);
+      for (int idx = 0; idx < OZ_S; ++idx) {
+        const int l = idx + 2;
+        if (l <= 7) {
+          const int shift = 7 * (7 - l);
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < 4; ++t)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) I[t][r] += ((long long)__float2int_rn(acc[idx][t][r])) << shift;
-      } else {
-        const float w = __int_as_float((127 - 7 * (l - 7)) << 23);
+            for (int r = 0; r < 4; ++r) I[t][r] += ((long long)__float2int_rn(acc[idx][t][r])) << shift;
+        } else {
+          const float w = __int_as_float((127 - 7 * (l - 7)) << 23);
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < 4; ++t)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) F[t][r] = fmaf(acc[idx][t][r], w, F[t][r]);
+            for (int r = 0; r < 4; ++r) F[t][r] = fmaf(acc[idx][t][r], w, F[t][r]);
+        }
       }
     }
+    // the buffer just read is the target of the next iteration's prefetch
     __syncthreads();
   }
   const int g = lane >> 2, c2 = (lane & 3) * 2;
@@ -332,7 +376,7 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
     DQ_KSCOPE(KF_SLICE, st);
     oz_slice_kernel<<<stiles, 256, 0, st>>>(oa, ob);
   }
-  const int smem = 2 * OZ_S * OZ_BM * OZ_LD * (int)sizeof(unsigned short);
+  const int smem = 2 * OZ_BUF * (int)sizeof(unsigned short);  // two staging buffers
   e = ensure_smem_attr((const void *)oz_gemm_rb_kernel, smem);
   if (e != cudaSuccess) return e;
   // one CTA per SM (shared memory); split K when the tiles do not fill the GPU
