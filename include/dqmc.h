@@ -203,14 +203,17 @@ dqmc_status dqmc_set_field(dqmc_ctx *ctx, const int8_t *s);
  * [1, M] or target values other than +-1. */
 dqmc_status dqmc_replay(dqmc_ctx *ctx, const int8_t *target, int slice, double *G_out);
 
-/* Checkpoint: parameters, options, field, sweep counter, statistics and bins.
- * G is recomputed on load. Binary file; DQMC_EINVAL if the file does not match
- * the context's (L, beta, dtau, U, mu). */
+/* Checkpoint: parameters, the options k, n_stab, precision, chain,
+ * site_offsets and bin, the field, the sweep counter, statistics and bins (the
+ * other options keep the loading context's values). G is recomputed on load.
+ * Binary file; DQMC_EINVAL if the file does not match the context's
+ * (L, beta, dtau, U, mu) or cannot be opened. */
 dqmc_status dqmc_save(dqmc_ctx *ctx, const char *path);
 dqmc_status dqmc_load(dqmc_ctx *ctx, const char *path);
 
-/* Batched independent chains (Sec. III runs many independent Markov chains;
- * here several of possibly different L on one GPU). dqmc_batch_create makes n
+/* Batched independent chains (several Markov chains, of possibly different
+ * L, sharing one GPU; the paper does not say how it used its cores, DQMC
+ * usually parallelises over independent chains). dqmc_batch_create makes n
  * contexts from params, n rows of (L, beta, dtau, U, mu, seed) doubles (L and
  * seed integral), into the caller's array out[n]; chain i gets chain id i
  * and its own non-blocking CUDA stream (destroyed with the context). Each
@@ -224,7 +227,11 @@ dqmc_status dqmc_load(dqmc_ctx *ctx, const char *path);
 dqmc_status dqmc_batch_create(int n, const double *params, dqmc_ctx **out);
 dqmc_status dqmc_batch_sweep(dqmc_ctx **ctxs, int n, int n_sweeps, int measure);
 
+/* Message of the last failure on the calling host thread ("" if none); valid
+ * until the thread's next failing call. */
 const char *dqmc_last_error(void);
+/* Synchronise the context's streams, free its device memory (through the
+ * allocator callbacks when set) and the context. NULL is ignored. */
 void dqmc_destroy(dqmc_ctx *ctx);
 
 /* Library version string. */
