@@ -1286,16 +1286,32 @@ dqmc_status dqmc_load(dqmc_ctx *c, const char *path) {
     std::fclose(fp);
     return fail(DQMC_EINVAL, "checkpoint parameters do not match this context");
   }
+  // a damaged file must not reach the allocator or the kernels
+  if (!valid_k(opt[0]) || opt[1] < 1 || opt[2] < 0 || opt[2] > 2 || opt[3] < 0 || opt[3] > 0xffffff ||
+      opt[5] < 1 || st[0] < 0 || st[1] < 0 || st[2] < 0 || st[2] > st[1] || !(md >= 0.0)) {
+    std::fclose(fp);
+    return fail(DQMC_EINVAL, "corrupt checkpoint header");
+  }
   if (c->allocated && (opt[0] != c->k || opt[1] != c->n_stab || opt[2] != c->precision || opt[3] != c->chain)) {
     std::fclose(fp);
     return fail(DQMC_ESTATE, "checkpoint options differ from an already started context");
   }
   std::vector<int8_t> f((size_t)c->M * c->N);
   ok = std::fread(f.data(), 1, f.size(), fp) == f.size() && std::fread(&ns, sizeof(long), 1, fp) == 1;
-  std::vector<std::array<double, 6>> smp(ok ? ns : 0);
+  // the samples must be exactly what is left of the file
+  if (ok) {
+    const long pos = std::ftell(fp);
+    ok = pos >= 0 && std::fseek(fp, 0, SEEK_END) == 0;
+    const long end = ok ? std::ftell(fp) : -1;
+    ok = ok && end >= pos && ns >= 0 && ns <= (end - pos) / (long)(6 * sizeof(double)) &&
+         (end - pos) == ns * (long)(6 * sizeof(double)) && std::fseek(fp, pos, SEEK_SET) == 0;
+  }
+  std::vector<std::array<double, 6>> smp(ok ? (size_t)ns : 0);
   for (long q = 0; ok && q < ns; ++q) ok = std::fread(smp[q].data(), sizeof(double), 6, fp) == 6;
   std::fclose(fp);
-  if (!ok) return fail(DQMC_EINVAL, "truncated checkpoint");
+  if (!ok) return fail(DQMC_EINVAL, "truncated or damaged checkpoint");
+  for (const int8_t v : f)
+    if (v != 1 && v != -1) return fail(DQMC_EINVAL, "checkpoint field values must be +1 or -1");
   if (!c->allocated) {
     c->k = opt[0];
     c->n_stab = opt[1];

@@ -115,3 +115,31 @@ def test_batch_create_validation(lib):
     assert lib.dqmc_batch_sweep(None, 1, 1, 0) == 1
     dup = (C.c_void_p * 2)(C.c_void_p(16), C.c_void_p(16))
     assert lib.dqmc_batch_sweep(dup, 2, 1, 0) == 1          # the same context twice
+
+
+def _checkpoint(M=20, N=48, k=8, n_stab=10, prec=0, chain=0, bin_=10, st=(2, 1920, 900), md=1e-9,
+                field=None, ns=0, extra=b""):
+    import struct
+    f = bytes([1] * (M * N)) if field is None else field
+    return (b"DQMCGB31" + struct.pack("<5d", 4, 2.0, 0.1, -4.0, -1.0) + struct.pack("<Q", 1)
+            + struct.pack("<7i", k, n_stab, prec, chain, 1, bin_, 0) + struct.pack("<3q", *st)
+            + struct.pack("<d", md) + f + struct.pack("<q", ns)
+            + b"\0" * (48 * ns if 0 <= ns <= 100 else 0) + extra)
+
+
+@pytest.mark.parametrize("kw,why", [
+    (dict(k=7), "header"), (dict(n_stab=0), "header"), (dict(prec=5), "header"),
+    (dict(bin_=0), "header"), (dict(st=(2, 10, 11)), "header"), (dict(md=float("nan")), "header"),
+    (dict(ns=-1), "damaged"), (dict(ns=10**15), "damaged"), (dict(ns=1, extra=b"x"), "damaged"),
+    (dict(field=bytes([1] * 959 + [0])), "+1 or -1"),
+])
+def test_load_rejects_damaged_checkpoints_before_any_device_work(lib, tmp_path, kw, why):
+    """A damaged checkpoint (bad options, counters, sample count or field
+    values) is refused with DQMC_EINVAL before anything is allocated."""
+    st, h = _create(lib)
+    assert st == 0
+    path = tmp_path / "ck.bin"
+    path.write_bytes(_checkpoint(**kw))
+    assert lib.dqmc_load(h, str(path).encode()) == 1
+    assert why in lib.dqmc_last_error().decode()
+    lib.dqmc_destroy(h)
