@@ -47,7 +47,8 @@ typedef struct dqmc_ctx dqmc_ctx;
 typedef enum {
   DQMC_OK = 0,
   DQMC_EINVAL = 1,    /* bad argument (size, sign of U, unsupported L, null pointer) */
-  DQMC_ENOMEM = 2,    /* device or host allocation failed */
+  DQMC_ENOMEM = 2,    /* device or host allocation failed, or the host refused another
+                         resource (no C++ exception crosses this interface) */
   DQMC_ECUDA = 3,     /* a CUDA runtime call or kernel failed */
   DQMC_ENUMERIC = 4,  /* non-positive or non-finite acceptance ratio, drift above the hard limit */
   DQMC_ETIMEOUT = 5,  /* a bounded device wait gave up */

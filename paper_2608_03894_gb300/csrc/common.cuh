@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
+#include <new>
 #include <string>
 
 #include "../../include/dqmc.h"
@@ -15,6 +17,23 @@ namespace dq {
 void set_error(const std::string &msg);
 dqmc_status fail(dqmc_status st, const std::string &msg);
 dqmc_status cuda_fail(cudaError_t e, const char *what);
+
+// Records msg without throwing (used where a C++ exception was caught).
+dqmc_status fail_host(dqmc_status st, const char *msg) noexcept;
+
+// Tail of the function-try-block of every C ABI entry point: no C++
+// exception (a failed host allocation or thread creation) crosses the C
+// boundary; it becomes DQMC_ENOMEM with its message.
+#define DQ_API_CATCH                                                              \
+  catch (const std::bad_alloc &) {                                                \
+    return ::dq::fail_host(DQMC_ENOMEM, "host memory exhausted");                 \
+  }                                                                               \
+  catch (const std::exception &_x) {                                              \
+    return ::dq::fail_host(DQMC_ENOMEM, _x.what());                               \
+  }                                                                               \
+  catch (...) {                                                                   \
+    return ::dq::fail_host(DQMC_ENOMEM, "host exception");                        \
+  }
 
 #define DQ_CUDA(call)                                     \
   do {                                                    \

@@ -20,6 +20,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -34,6 +35,13 @@ static thread_local std::string g_last_error;
 void set_error(const std::string &msg) { g_last_error = msg; }
 dqmc_status fail(dqmc_status st, const std::string &msg) {
   set_error(msg);
+  return st;
+}
+dqmc_status fail_host(dqmc_status st, const char *msg) noexcept {
+  try {
+    g_last_error = std::string("host: ") + msg;
+  } catch (...) {
+  }
   return st;
 }
 dqmc_status cuda_fail(cudaError_t e, const char *what) {
@@ -894,7 +902,7 @@ const char *dqmc_version(void) { return "dqmc-gb300 0.1 (sm_103a)"; }
 const char *dqmc_last_error(void) { return g_last_error.c_str(); }
 
 dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, uint64_t seed,
-                        dqmc_ctx **out) {
+                        dqmc_ctx **out) try {
   if (!out) return fail(DQMC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!supported_L(L)) return fail(DQMC_EINVAL, "unsupported L (supported: 1,2,3,4,6,8,12,16,24,36)");
@@ -918,9 +926,9 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
   if (c->N < c->k) c->k = 4;
   *out = c;
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) {
+dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
   DQ_CHECK(check_ctx(c));
   if (!key) return fail(DQMC_EINVAL, "key is NULL");
   const std::string k(key);
@@ -977,16 +985,16 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) {
     return fail(DQMC_EINVAL, "unknown option '" + k + "'");
   }
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_set_stream(dqmc_ctx *c, void *stream) {
+dqmc_status dqmc_set_stream(dqmc_ctx *c, void *stream) try {
   DQ_CHECK(check_ctx(c));
   c->stream = static_cast<cudaStream_t>(stream);
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
 dqmc_status dqmc_set_allocator(dqmc_ctx *c, void *(*alloc)(size_t, void *),
-                               void (*release)(void *, void *), void *user) {
+                               void (*release)(void *, void *), void *user) try {
   DQ_CHECK(check_ctx(c));
   if (c->allocated) return fail(DQMC_ESTATE, "allocator must be set before the first allocation");
   if ((alloc == nullptr) != (release == nullptr)) return fail(DQMC_EINVAL, "alloc and release go together");
@@ -994,9 +1002,9 @@ dqmc_status dqmc_set_allocator(dqmc_ctx *c, void *(*alloc)(size_t, void *),
   c->ufree = release;
   c->uuser = user;
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_sweep(dqmc_ctx *c, int n_sweeps, int measure) {
+dqmc_status dqmc_sweep(dqmc_ctx *c, int n_sweeps, int measure) try {
   DQ_CHECK(check_ctx(c));
   if (n_sweeps < 0) return fail(DQMC_EINVAL, "n_sweeps must be >= 0");
   DQ_CHECK(ensure_ready(c));
@@ -1021,9 +1029,9 @@ dqmc_status dqmc_sweep(dqmc_ctx *c, int n_sweeps, int measure) {
     c->meas_n = 0;
   }
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_green(dqmc_ctx *c, int slice, double *G_out) {
+dqmc_status dqmc_green(dqmc_ctx *c, int slice, double *G_out) try {
   DQ_CHECK(check_ctx(c));
   if (!G_out) return fail(DQMC_EINVAL, "G_out is NULL");
   if (slice < 0 || slice > c->M) return fail(DQMC_EINVAL, "slice out of range");
@@ -1045,9 +1053,9 @@ dqmc_status dqmc_green(dqmc_ctx *c, int slice, double *G_out) {
   CK(cudaMemcpyAsync(G_out, c->Xp, (size_t)c->N * c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_get_running_green(dqmc_ctx *c, double *G_out, int *slice) {
+dqmc_status dqmc_get_running_green(dqmc_ctx *c, double *G_out, int *slice) try {
   DQ_CHECK(check_ctx(c));
   if (!G_out) return fail(DQMC_EINVAL, "G_out is NULL");
   PhaseTimer tm(c);
@@ -1062,9 +1070,9 @@ dqmc_status dqmc_get_running_green(dqmc_ctx *c, double *G_out, int *slice) {
   CK(cudaStreamSynchronize(c->stream));
   if (slice) *slice = c->cur_slice;
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_measure(dqmc_ctx *c, dqmc_obs *o) {
+dqmc_status dqmc_measure(dqmc_ctx *c, dqmc_obs *o) try {
   DQ_CHECK(check_ctx(c));
   if (!o) return fail(DQMC_EINVAL, "out is NULL");
   std::memset(o, 0, sizeof(*o));
@@ -1139,9 +1147,9 @@ dqmc_status dqmc_measure(dqmc_ctx *c, dqmc_obs *o) {
     o->P_err = std::nan("");
   }
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_get_stats(dqmc_ctx *c, dqmc_stats *o) {
+dqmc_status dqmc_get_stats(dqmc_ctx *c, dqmc_stats *o) try {
   if (!c) return fail(DQMC_EINVAL, "null context");
   if (!o) return fail(DQMC_EINVAL, "out is NULL");
   o->sweeps = c->sweeps;
@@ -1161,18 +1169,18 @@ dqmc_status dqmc_get_stats(dqmc_ctx *c, dqmc_stats *o) {
   }
   o->launches = c->launches;
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_get_field(dqmc_ctx *c, int8_t *s_out) {
+dqmc_status dqmc_get_field(dqmc_ctx *c, int8_t *s_out) try {
   DQ_CHECK(check_ctx(c));
   if (!s_out) return fail(DQMC_EINVAL, "s_out is NULL");
   DQ_CHECK(ensure_alloc(c));
   CK(cudaMemcpyAsync(s_out, c->field, (size_t)c->M * c->N, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_set_field(dqmc_ctx *c, const int8_t *s) {
+dqmc_status dqmc_set_field(dqmc_ctx *c, const int8_t *s) try {
   DQ_CHECK(check_ctx(c));
   if (!s) return fail(DQMC_EINVAL, "s is NULL");
   const size_t n = (size_t)c->M * c->N;
@@ -1184,9 +1192,9 @@ dqmc_status dqmc_set_field(dqmc_ctx *c, const int8_t *s) {
   CK(cudaStreamSynchronize(c->stream));
   c->ready = false;
   return ensure_ready(c);
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_replay(dqmc_ctx *c, const int8_t *target, int slice, double *G_out) {
+dqmc_status dqmc_replay(dqmc_ctx *c, const int8_t *target, int slice, double *G_out) try {
   DQ_CHECK(check_ctx(c));
   if (!target || !G_out) return fail(DQMC_EINVAL, "target and G_out must not be NULL");
   if (slice < 1 || slice > c->M) return fail(DQMC_EINVAL, "slice must be in [1, M]");
@@ -1235,9 +1243,9 @@ dqmc_status dqmc_replay(dqmc_ctx *c, const int8_t *target, int slice, double *G_
   c->ready = false;
   c->cur_slice = 0;
   return read_status(c);
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_save(dqmc_ctx *c, const char *path) {
+dqmc_status dqmc_save(dqmc_ctx *c, const char *path) try {
   DQ_CHECK(check_ctx(c));
   if (!path) return fail(DQMC_EINVAL, "path is NULL");
   DQ_CHECK(ensure_alloc(c));
@@ -1261,9 +1269,9 @@ dqmc_status dqmc_save(dqmc_ctx *c, const char *path) {
   std::fclose(fp);
   if (!ok) return fail(DQMC_EINVAL, "short write");
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_load(dqmc_ctx *c, const char *path) {
+dqmc_status dqmc_load(dqmc_ctx *c, const char *path) try {
   DQ_CHECK(check_ctx(c));
   if (!path) return fail(DQMC_EINVAL, "path is NULL");
   FILE *fp = std::fopen(path, "rb");
@@ -1333,9 +1341,9 @@ dqmc_status dqmc_load(dqmc_ctx *c, const char *path) {
   c->samples = smp;
   c->ready = false;
   return ensure_ready(c);
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_batch_create(int n, const double *params, dqmc_ctx **out) {
+dqmc_status dqmc_batch_create(int n, const double *params, dqmc_ctx **out) try {
   if (n < 1 || !params || !out) return fail(DQMC_EINVAL, "need n >= 1, params and out");
   for (int i = 0; i < n; ++i) out[i] = nullptr;
   for (int i = 0; i < n; ++i) {
@@ -1373,9 +1381,9 @@ dqmc_status dqmc_batch_create(int n, const double *params, dqmc_ctx **out) {
     }
   }
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_batch_sweep(dqmc_ctx **ctxs, int n, int n_sweeps, int measure) {
+dqmc_status dqmc_batch_sweep(dqmc_ctx **ctxs, int n, int n_sweeps, int measure) try {
   if (n < 1 || !ctxs) return fail(DQMC_EINVAL, "need n >= 1 and the contexts");
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(DQMC_EINVAL, "context " + std::to_string(i) + " is NULL");
@@ -1386,17 +1394,33 @@ dqmc_status dqmc_batch_sweep(dqmc_ctx **ctxs, int n, int n_sweeps, int measure) 
   std::vector<std::string> errs(n);
   std::vector<std::thread> th;
   th.reserve(n);
-  for (int i = 0; i < n; ++i)
-    th.emplace_back([&, i] {
-      cudaSetDevice(ctxs[i]->device);
-      rs[i] = dqmc_sweep(ctxs[i], n_sweeps, measure);
-      if (rs[i] != DQMC_OK) errs[i] = g_last_error;
-    });
+  auto run = [&](int i) {
+    cudaSetDevice(ctxs[i]->device);
+    rs[i] = dqmc_sweep(ctxs[i], n_sweeps, measure);
+    if (rs[i] != DQMC_OK) errs[i] = g_last_error;
+  };
+  // chains [0, spawned) on their own threads; if the host refuses a thread,
+  // the rest run one after another on the calling thread (its current
+  // device restored afterwards), concurrently with the spawned ones
+  int spawned = 0;
+  for (; spawned < n; ++spawned) {
+    try {
+      th.emplace_back(run, spawned);
+    } catch (const std::system_error &) {
+      break;
+    }
+  }
+  if (spawned < n) {
+    int dev = 0;
+    const bool have_dev = cudaGetDevice(&dev) == cudaSuccess;
+    for (int i = spawned; i < n; ++i) run(i);
+    if (have_dev) cudaSetDevice(dev);
+  }
   for (auto &t : th) t.join();
   for (int i = 0; i < n; ++i)
     if (rs[i] != DQMC_OK) return fail(rs[i], "chain " + std::to_string(i) + ": " + errs[i]);
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
 void dqmc_destroy(dqmc_ctx *c) {
   if (!c) return;

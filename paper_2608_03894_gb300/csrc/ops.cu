@@ -68,42 +68,42 @@ extern "C" {
 
 dqmc_status dqmc_op_propagate_f64(int L, double scale, int side, const double *X, double *Y,
                                   int nvec, int ld, const double *pre, const double *post,
-                                  const double *vscale, void *stream) {
+                                  const double *vscale, void *stream) try {
   DQ_CHECK(check_prop(L, side, X, Y, nvec, ld));
   const void *E = nullptr;
   DQ_CHECK(op_table(L, scale, 0, &E));
   DQ_CUDA(launch_prop_f64(L, side, X, Y, nvec, ld, static_cast<const cpx<double> *>(E), pre, post,
                           vscale, static_cast<cudaStream_t>(stream)));
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
 dqmc_status dqmc_op_propagate_df(int L, double scale, int side, const double *X, double *Y,
                                  int nvec, int ld, const double *pre, const double *post,
-                                 const double *vscale, void *stream) {
+                                 const double *vscale, void *stream) try {
   DQ_CHECK(check_prop(L, side, X, Y, nvec, ld));
   const void *E = nullptr;
   DQ_CHECK(op_table(L, scale, 2, &E));
   DQ_CUDA(launch_prop_df(L, side, X, Y, nvec, ld, static_cast<const cpx<df64> *>(E), pre, post,
                          vscale, static_cast<cudaStream_t>(stream)));
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
 dqmc_status dqmc_op_propagate_f32(int L, double scale, int side, const float *X, float *Y,
                                   int nvec, int ld, const float *pre, const float *post,
-                                  const float *vscale, void *stream) {
+                                  const float *vscale, void *stream) try {
   DQ_CHECK(check_prop(L, side, X, Y, nvec, ld));
   const void *E = nullptr;
   DQ_CHECK(op_table(L, scale, 1, &E));
   DQ_CUDA(launch_prop_f32(L, side, X, Y, nvec, ld, static_cast<const cpx<float> *>(E), pre, post,
                           vscale, static_cast<cudaStream_t>(stream)));
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
 dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, int ld_g,
                                      int8_t *s, double lambda, uint64_t seed, uint32_t chain,
                                      uint32_t sweep_pass, int slice1, const uint8_t *forced,
                                      double *alpha, double *beta, int *accept_count, int *status,
-                                     void *stream) {
+                                     void *stream) try {
   if (N < 1 || kb < 1 || kb > 64 || site0 < 0 || site0 + kb > N)
     return fail(DQMC_EINVAL, "need 1 <= kb <= 64 and 0 <= site0, site0 + kb <= N");
   if (!g || !s || !alpha || !beta || !accept_count || !status) return fail(DQMC_EINVAL, "null pointer");
@@ -126,7 +126,7 @@ dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, 
   DQ_CUDA(launch_metropolis(a, g, false, s, forced, alpha, beta, accept_count, status, nullptr,
                             static_cast<cudaStream_t>(stream)));
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
 }  // extern "C"
 
@@ -156,25 +156,25 @@ extern "C" {
 
 dqmc_status dqmc_op_flush_f64(int N, int site0, int kb, double *G, const double *Gcol,
                               const double *Grow, const double *alpha, const double *beta,
-                              const int *accept_count, void *stream) {
+                              const int *accept_count, void *stream) try {
   return op_flush<double>(N, site0, kb, G, Gcol, Grow, alpha, beta, accept_count, false, stream);
-}
+} DQ_API_CATCH
 
 dqmc_status dqmc_op_flush_df(int N, int site0, int kb, double *G, const double *Gcol,
                              const double *Grow, const double *alpha, const double *beta,
-                             const int *accept_count, void *stream) {
+                             const int *accept_count, void *stream) try {
   return op_flush<double>(N, site0, kb, G, Gcol, Grow, alpha, beta, accept_count, true, stream);
-}
+} DQ_API_CATCH
 
 dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *Gcol,
                               const float *Grow, const double *alpha, const double *beta,
-                              const int *accept_count, void *stream) {
+                              const int *accept_count, void *stream) try {
   return op_flush<float>(N, site0, kb, G, Gcol, Grow, alpha, beta, accept_count, false, stream);
-}
+} DQ_API_CATCH
 
 dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, double alpha,
                              const double *A, int lda, const double *B, int ldb, double beta,
-                             double *C, int ldc, void *stream) {
+                             double *C, int ldc, void *stream) try {
   if (mode < 0 || mode > 2) return fail(DQMC_EINVAL, "mode must be 0 (FP64), 1 (double-float) or 2 (digit slices)");
   if (M < 0 || N < 0 || K < 0) return fail(DQMC_EINVAL, "negative size");
   if ((M && N && K) && (!A || !B)) return fail(DQMC_EINVAL, "null operand");
@@ -203,9 +203,9 @@ dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, doub
   if (ex) cudaFreeAsync(ex, st);
   if (e != cudaSuccess) return cuda_fail(e, "gemm");
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
-dqmc_status dqmc_op_measure(int L, const double *G, int site_offsets, double *out, void *stream) {
+dqmc_status dqmc_op_measure(int L, const double *G, int site_offsets, double *out, void *stream) try {
   if (!supported_L(L)) return fail(DQMC_EINVAL, "unsupported L");
   if (!G || !out) return fail(DQMC_EINVAL, "null pointer");
   const int N = 3 * L * L;
@@ -257,6 +257,6 @@ dqmc_status dqmc_op_measure(int L, const double *G, int site_offsets, double *ou
   cudaFree(dn);
   if (e != cudaSuccess) return cuda_fail(e, "dqmc_op_measure");
   return DQMC_OK;
-}
+} DQ_API_CATCH
 
 }  // extern "C"

@@ -50,7 +50,7 @@ using namespace dq;
 extern "C" dqmc_status dqmc_op_flush_f64_noalloc(int N, int site0, int kb, double *G,
                                                  const double *Gcol, const double *Grow,
                                                  const double *alpha, const double *beta,
-                                                 const int *accept_count, void *stream) {
+                                                 const int *accept_count, void *stream) try {
   if (N < 1 || kb < 1 || kb > 64 || site0 < 0 || site0 + kb > N)
     return fail(DQMC_EINVAL, "need 1 <= kb <= 64 and 0 <= site0, site0 + kb <= N");
   if (!G || !Gcol || !Grow || !alpha || !beta || !accept_count) return fail(DQMC_EINVAL, "null pointer");
@@ -69,4 +69,4 @@ extern "C" dqmc_status dqmc_op_flush_f64_noalloc(int N, int site0, int kb, doubl
                                              nullptr, nullptr, false, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "flush");
   return DQMC_OK;
-}
+} DQ_API_CATCH
