@@ -184,8 +184,11 @@ dqmc_status dqmc_measure(dqmc_ctx *ctx, dqmc_obs *out);
 /* Statistics (see dqmc_stats). */
 dqmc_status dqmc_get_stats(dqmc_ctx *ctx, dqmc_stats *out);
 
-/* Copy the field out (M*N int8) or in. Setting the field rebuilds the stacks
- * and G at tau = 0 (values other than +-1 -> DQMC_EINVAL). */
+/* Copy the field out (M*N int8) or in. Setting a field rebuilds the stacks
+ * and G at tau = 0 (values other than +-1 -> DQMC_EINVAL). Setting the field
+ * the chain already holds at tau = 0 (e.g. the one dqmc_get_field returned
+ * after a sweep) is detected on the device and keeps the running G and the
+ * stacks as they are. */
 dqmc_status dqmc_get_field(dqmc_ctx *ctx, int8_t *s_out);
 dqmc_status dqmc_set_field(dqmc_ctx *ctx, const int8_t *s);
 

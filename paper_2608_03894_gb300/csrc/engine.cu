@@ -660,6 +660,15 @@ __global__ void flip_flags_kernel(const int8_t *field, const int8_t *target, lon
     flags[q] = field[q] != target[q] ? 1 : 0;
 }
 
+// *flag = 1 if the two fields differ anywhere (flag cleared by the caller)
+__global__ void field_differs_kernel(const int8_t *a, const int8_t *b, long n, int *flag) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
+    if (a[q] != b[q]) {
+      *flag = 1;
+      break;
+    }
+}
+
 __global__ void drift_max_kernel(const double *d, double *mx) {
   const double v = *d;
   if (v != v || v > *mx) *mx = v;
@@ -1188,7 +1197,28 @@ dqmc_status dqmc_set_field(dqmc_ctx *c, const int8_t *s) try {
     if (s[q] != 1 && s[q] != -1) return fail(DQMC_EINVAL, "field values must be +1 or -1");
   PhaseTimer tm(c);
   DQ_CHECK(ensure_alloc(c));
-  CK(cudaMemcpyAsync(c->field, s, n, cudaMemcpyHostToDevice, c->stream));
+  if (c->ready && c->cur_slice == 0) {
+    // Setting the state the chain is already in changes nothing: G and the
+    // UDV stacks stay valid. The new field is staged on the device and
+    // compared there; only a different field is installed and rebuilt from.
+    if (!c->flip_flags) DQ_CHECK(ctx_alloc_n(c, &c->flip_flags, 2 * n));
+    int8_t *stage = reinterpret_cast<int8_t *>(c->flip_flags + n);
+    CK(cudaMemcpyAsync(stage, s, n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->status + 3, 0, sizeof(int), c->stream));
+    {
+      DQ_KSCOPE(KF_OTHER, c->stream);
+      const int grid = (int)std::min<long>(4096, ((long)n + 255) / 256);
+      field_differs_kernel<<<grid, 256, 0, c->stream>>>(c->field, stage, (long)n, c->status + 3);
+      CK(cudaGetLastError());
+    }
+    int differs = 1;
+    CK(cudaMemcpyAsync(&differs, c->status + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!differs) return DQMC_OK;
+    CK(cudaMemcpyAsync(c->field, stage, n, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(c->field, s, n, cudaMemcpyHostToDevice, c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
   c->ready = false;
   return ensure_ready(c);

@@ -465,3 +465,26 @@ def test_digit_slice_gemm_accuracy_is_relative_to_row_scale(pkg):
     rowmax = np.abs(A).max(axis=1, keepdims=True)
     colmax = np.abs(B).max(axis=0, keepdims=True)
     assert np.max(np.abs(C.cpu().numpy() - ref) / (rowmax * colmax)) < K * 2.0 ** -55
+
+
+def test_set_field_to_the_current_state_keeps_g(pkg):
+    """Setting the field the chain is already in is a no-op (the running G is
+    kept bit for bit); a different field is installed and G rebuilt from it
+    (equal to the oracle's from-scratch G at slice 0)."""
+    par = dict(L=4, beta=2.0, dtau=0.1, U=-4.0, mu=-1.0)
+    m = omodel.Model(**par)
+    with pkg.DQMC(**par, seed=1, k=8, n_stab=10, precision="fp64") as d:
+        d.sweep(1)
+        G0, sl0 = d.running_green()
+        f = d.field
+        d.field = f
+        G1, sl1 = d.running_green()
+        assert sl0 == sl1 == 0 and np.array_equal(G0, G1)
+        f2 = f.copy()
+        f2[0, 0] = -f2[0, 0]
+        d.field = f2
+        G2, sl2 = d.running_green()
+        assert sl2 == 0 and np.array_equal(d.field, f2)
+        assert np.max(np.abs(G2 - ogreen.green_udv(m, f2, 0))) < 1e-10
+        d.sweep(1)
+        assert d.stats()["max_drift"] < 1e-6
