@@ -240,6 +240,17 @@ def run_micro(args):
     print(json.dumps({"micro": "prop", "results": out}), flush=True)
 
 
+def soft(fn):
+    """Run an optional leg of the bench; an exception becomes {"error": ...} in
+    the JSON line instead of losing the line (the timed value stands alone).
+    A leg that returns a dict is passed through; anything else is wrapped."""
+    try:
+        out = fn()
+    except Exception as exc:
+        return {"error": f"{type(exc).__name__}: {exc}"}
+    return out if isinstance(out, dict) else {"value": out}
+
+
 def replica(w, rank):
     """Replicas: every rank runs its own chain, seed + rank and chain id rank
     (independent Philox streams), no collective on the data path."""
@@ -304,8 +315,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- end to end through the public API: field in from pinned host memory,
     # one sweep with measurements, field and observables back to the host
-    e2e = None
-    if not args.no_e2e:
+    def e2e_leg():
         lib = _lib.load()
         fin = torch.empty((M, N), dtype=torch.int8, pin_memory=True)
         fout = torch.empty((M, N), dtype=torch.int8, pin_memory=True)
@@ -323,76 +333,90 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         te = max_over_ranks(te, dist, "cuda")
-        e2e = {"value": units_per_step * args.steps * world / te, "unit": UNIT,
-               "h2d_bytes_per_step": M * N, "d2h_bytes_per_step": M * N + 6 * 8 * (-(-M // w["n_stab"]))}
+        return {"value": units_per_step * args.steps * world / te, "unit": UNIT,
+                "h2d_bytes_per_step": M * N, "d2h_bytes_per_step": M * N + 6 * 8 * (-(-M // w["n_stab"]))}
+
+    e2e = None if args.no_e2e else soft(e2e_leg)
 
     # ---- one extra sweep with per-kernel-family CUDA events for the roofline
-    d.set_option("timing", 2)
-    s0 = d.stats()
-    d.sweep(1)
-    s1 = d.stats()
-    d.set_option("timing", 0)
-    fam = {}
-    for f in s1["ms_kernel"]:
-        dt = s1["ms_kernel"][f] - s0["ms_kernel"][f]
-        n = s1["n_kernel"][f] - s0["n_kernel"][f]
-        fam[f] = {"ms": dt, "launches": n, "flops": s1["flops_kernel"][f] - s0["flops_kernel"][f],
-                  "bytes": s1["bytes_kernel"][f] - s0["bytes_kernel"][f]}
-    total_ms = sum(v["ms"] for v in fam.values())
-    # the flush's work is counted at m = k flips per block on the host; the
-    # true rank is the number of accepted flips: rescale to the accepted count
-    acc = s1["accepted"] - s0["accepted"]
-    prop_n = s1["proposed"] - s0["proposed"]
-    if fam["flush"]["flops"] > 0 and prop_n > 0:
-        fam["flush"]["flops"] *= acc / float(prop_n)
-    # dominant kernel family on the critical path ("other" is many small kernels;
-    # the look-ahead Metropolis overlaps the flush)
-    dom = max(("prop", "flush", "gemm", "qr_panel"), key=lambda f: fam[f]["ms"])
-    peaks, peak_src = load_peaks()
-    mhz_max = peaks.get("sm_max_mhz", 2070.0)
-    fd = fam[dom]
-    per_launch_s = fd["ms"] / 1000.0 / max(1, fd["launches"])
-    mixed = w["precision"] == "mixed"
-    if dom == "prop":
-        achieved = fd["bytes"] / max(1, fd["launches"]) / per_launch_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "peak_source": f"{peak_src} copy bandwidth"}
-    elif dom == "gemm" and mixed:
-        # digit slices: 45 bf16 products per FP64-equivalent multiply-add
-        achieved = 45.0 * fd["flops"] / max(1, fd["launches"]) / per_launch_s / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops_sustained", 1700.0),
-                "unit": "TFLOP/s", "peak_source": f"{peak_src} sustained bf16 (cuBLAS); bf16 MMA rate of the "
-                                                   "digit-slice GEMM = 45 x its FP64-equivalent rate"}
-    elif dom == "flush" and mixed:
-        # double-float MAC = 12 FP32 instructions: peak FP64-equivalent rate = FP32 FMA issue rate / 12 x 2
-        achieved = fd["flops"] / max(1, fd["launches"]) / per_launch_s / 1e12
-        peak = alu_peak_tflops("fp32", mhz_max) / 12.0
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"FP64-equivalent double-float rate: 152 SMs x 128 FP32 lanes x {mhz_max:.0f} MHz "
-                               "/ 12 instructions per multiply-add x 2"}
+    def roofline_leg():
+        d.set_option("timing", 2)
+        s0 = d.stats()
+        d.sweep(1)
+        s1 = d.stats()
+        d.set_option("timing", 0)
+        fam = {}
+        for f in s1["ms_kernel"]:
+            dt = s1["ms_kernel"][f] - s0["ms_kernel"][f]
+            n = s1["n_kernel"][f] - s0["n_kernel"][f]
+            fam[f] = {"ms": dt, "launches": n, "flops": s1["flops_kernel"][f] - s0["flops_kernel"][f],
+                      "bytes": s1["bytes_kernel"][f] - s0["bytes_kernel"][f]}
+        total_ms = sum(v["ms"] for v in fam.values())
+        # the flush's work is counted at m = k flips per block on the host; the
+        # true rank is the number of accepted flips: rescale to the accepted count
+        acc = s1["accepted"] - s0["accepted"]
+        prop_n = s1["proposed"] - s0["proposed"]
+        if fam["flush"]["flops"] > 0 and prop_n > 0:
+            fam["flush"]["flops"] *= acc / float(prop_n)
+        # dominant kernel family on the critical path ("other" is many small kernels;
+        # the look-ahead Metropolis overlaps the flush)
+        dom = max(("prop", "flush", "gemm", "qr_panel"), key=lambda f: fam[f]["ms"])
+        peaks, peak_src = load_peaks()
+        mhz_max = peaks.get("sm_max_mhz", 2070.0)
+        fd = fam[dom]
+        per_launch_s = fd["ms"] / 1000.0 / max(1, fd["launches"])
+        mixed = w["precision"] == "mixed"
+        if dom == "prop":
+            achieved = fd["bytes"] / max(1, fd["launches"]) / per_launch_s / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "peak_source": f"{peak_src} copy bandwidth"}
+        elif dom == "gemm" and mixed:
+            # digit slices: 45 bf16 products per FP64-equivalent multiply-add
+            achieved = 45.0 * fd["flops"] / max(1, fd["launches"]) / per_launch_s / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops_sustained", 1700.0),
+                    "unit": "TFLOP/s", "peak_source": f"{peak_src} sustained bf16 (cuBLAS); bf16 MMA rate of the "
+                                                       "digit-slice GEMM = 45 x its FP64-equivalent rate"}
+        elif dom == "flush" and mixed:
+            # double-float MAC = 12 FP32 instructions: peak FP64-equivalent rate = FP32 FMA issue rate / 12 x 2
+            achieved = fd["flops"] / max(1, fd["launches"]) / per_launch_s / 1e12
+            peak = alu_peak_tflops("fp32", mhz_max) / 12.0
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": f"FP64-equivalent double-float rate: 152 SMs x 128 FP32 lanes x {mhz_max:.0f} MHz "
+                                   "/ 12 instructions per multiply-add x 2"}
+        else:
+            achieved = fd["flops"] / max(1, fd["launches"]) / per_launch_s / 1e12
+            peak = alu_peak_tflops("fp64", mhz_max)
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": f"fp64 issue rate x 152 SMs x {mhz_max:.0f} MHz"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["kernel"] = dom
+        roof["traffic"] = None
+        roof["share_of_device_time"] = fd["ms"] / max(total_ms, 1e-9)
+        return fam, roof
+
+    fam, roof = {}, None
+    r = soft(roofline_leg)
+    if "error" in r:
+        roof = r
     else:
-        achieved = fd["flops"] / max(1, fd["launches"]) / per_launch_s / 1e12
-        peak = alu_peak_tflops("fp64", mhz_max)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"fp64 issue rate x 152 SMs x {mhz_max:.0f} MHz"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom
-    roof["traffic"] = None
-    roof["share_of_device_time"] = fd["ms"] / max(total_ms, 1e-9)
+        fam, roof = r["value"]
 
     # FFT propagation alone on a stacked operand larger than L2 (HBM roofline of
     # the propagation kernels, FP32 / double-float / FP64 arithmetic)
     fft = None
     if rank == 0:
-        fft = []
-        for prec in ("fp32", "df", "fp64"):
+        hbm = load_peaks()[0]["hbm_gbs"]
+
+        def fft_leg(prec):
             r = prop_microbench(L, prec, max(1, (800 << 20) // (N * N * 4)))
-            r["frac_of_hbm"] = round(r["GB_s"] / peaks["hbm_gbs"], 3)
-            fft.append(r)
+            r["frac_of_hbm"] = round(r["GB_s"] / hbm, 3)
+            return r
+
+        fft = [soft(lambda p=prec: fft_leg(p)) for prec in ("fp32", "df", "fp64")]
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_oracle_sample(w, budget_s=args.cpu_budget)
+        cpu = soft(lambda: cpu_oracle_sample(w, budget_s=args.cpu_budget))
 
     if rank == 0:
         line = {
