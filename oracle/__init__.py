@@ -29,6 +29,10 @@ attractive Hubbard model on the kagome lattice"):
   kinetic energy.
 * ``fock``     -- exact diagonalisation and Fock-space Trotter products on
   tiny tori (3 and 6 sites), and the brute-force sum over all HS fields.
+* ``pqmc``     -- the projector (zero-temperature) variant of the paper
+  (Sec. II): trial Slater determinant from the lowest N_occ eigenstates of
+  K, G = I - R (L R)^{-1} L from orthonormal N x N_occ stacks, the same
+  sweep and proposals.
 
 Pins (tests marked ``not gpu``) tie every function to something other than
 itself: the textbook kagome band structure, scipy's Pade ``expm``, the U=0
@@ -37,4 +41,4 @@ convergence to exact diagonalisation, an exact-weight histogram of the Markov
 chain, and the Philox known-answer vectors.
 """
 
-from . import lattice, philox, model, green, measure, fock, dqmc  # noqa: F401
+from . import lattice, philox, model, green, measure, fock, dqmc, pqmc  # noqa: F401

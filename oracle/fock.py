@@ -191,6 +191,68 @@ class Sectors:
         return out, float(np.real(Z))
 
 
+    def _green_up(self, left, right, norm, nu, nd):
+        """<c_i c_j^+> (spin up) = delta_ij - <c_j^+ c_i> between two sector vectors."""
+        Id = np.eye(len(self.idx[nd]))
+        G = np.eye(self.N)
+        for i in range(self.N):
+            for j in range(self.N):
+                G[i, j] -= float(left @ (np.kron(self.h[nu][j][i], Id) @ right)) / norm
+        return G
+
+    def _expect(self, left, right, n, with_green):
+        norm = float(left @ right)
+        out = {}
+        for k, O in self._ops(n, n).items():
+            out[k] = float("nan") if O is None else float(np.real(left @ (O @ right))) / norm
+        if with_green:
+            out["G"] = self._green_up(left, right, norm, n, n)
+        return out, norm
+
+    def slater(self, P):
+        """Fock vector (one species, sector n = P.shape[1]) of the Slater
+        determinant of P's columns: the unique ground state of
+        -sum_ij (P P^T)_ij c+_i c_j with n particles (energy -n, gap 1)."""
+        n = P.shape[1]
+        Pp = P @ P.T
+        H = -sum(Pp[i, j] * self.h[n][i][j] for i in range(self.N) for j in range(self.N))
+        w, V = np.linalg.eigh(H)
+        if len(w) > 1 and w[1] - w[0] < 0.5:
+            raise ValueError("P does not define a unique Slater determinant")
+        return V[:, 0]
+
+    def pqmc(self, P, l, M=None, with_green=False):
+        """Projector averages <Psi_T| X^{M-l} O X^l |Psi_T> / <Psi_T| X^M |Psi_T>,
+        X = e^{-dtau(U_hat - mu N_hat)} e^{-dtau K_hat}, |Psi_T> the Slater
+        determinant of P for both species (sector (n, n), n = N_occ); the
+        observable sits at slice l, where G(tau_l) = I - R (L R)^{-1} L."""
+        m = self.model
+        M = m.M if M is None else M
+        dtau = m.beta / M
+        n = P.shape[1]
+        psi1 = self.slater(P)
+        psi = np.kron(psi1, psi1)
+        E = sla.expm(-dtau * self.k[n])
+        X = np.exp(-dtau * self._pot_diag(n, n))[:, None] * np.kron(E, E)
+        right = psi.copy()
+        for _ in range(l):
+            right = X @ right
+        left = psi.copy()
+        for _ in range(M - l):
+            left = X.T @ left
+        return self._expect(left, right, n, with_green)
+
+    def ground(self, n, with_green=False):
+        """Ground-state averages of H in the (n, n) sector (exact diagonalisation)."""
+        H = self._kin(n, n) + np.diag(self._pot_diag(n, n))
+        w, V = np.linalg.eigh(H)
+        if len(w) > 1 and w[1] - w[0] < 1e-9:
+            raise ValueError("degenerate ground state in the (n, n) sector")
+        v = V[:, 0]
+        out, _ = self._expect(v, v, n, with_green)
+        return out, float(w[0])
+
+
 def brute_force_hs(model, obs=None, with_green=False):
     """Sum over all 2^{N M} Ising fields: returns (weighted Wick averages,
     sum_s w_s). Weight w_s = prod e^{-lambda s} det(I + B_M ... B_1)^2.
