@@ -332,6 +332,18 @@ dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, doub
                              const double *A, int lda, const double *B, int ldb, double beta,
                              double *C, int ldc, void *stream);
 
+/* Trial orbitals of the projector (zero-temperature) variant, Sec. II: an
+ * orthonormal real basis of the lowest n_occ eigenstates of
+ * K + eps diag(+1, 0, -1) (sublattices A, B, C; t = 1), the filling being
+ * rho = 2 n_occ / N. eps splits the Dirac-point degeneracy of the closed shell
+ * at rho = 2/3 when 3 | L (1e-4 is the reading used here); 0 is allowed when
+ * the shell is closed without it. Host-only (no device work): P_out is a
+ * caller-owned host buffer of N * n_occ doubles, row-major (site index
+ * (x1 L + x2) 3 + a), built from the momentum blocks of Eq. 4. Open shell (the
+ * n_occ-th and next level closer than 1e-9, or a pair k, -k split) or
+ * 1 <= n_occ < N violated -> DQMC_EINVAL. */
+dqmc_status dqmc_op_trial_state(int L, int n_occ, double eps, double *P_out);
+
 /* Equal-time estimator sums from one FP64 G (N x N row-major, device): writes
  * out[6] (host) = S_pair_G, S_pair_dk, phi2_G, phi2_K, density, ekin, with the
  * same definitions and phase conventions as dqmc_obs (site_offsets as the

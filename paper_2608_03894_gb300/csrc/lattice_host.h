@@ -29,4 +29,16 @@ void expm3(const cd A[3][3], cd E[3][3]);
 // keeps; 1/L^2 is the normalisation of the inverse 2D transform.
 std::vector<cd> block_exp_table(int L, double scale, double t = 1.0);
 
+// Eigen-decomposition A = Q diag(w) Q^H of a 3 x 3 Hermitian matrix (Jacobi).
+void eigh3(const cd A[3][3], double w[3], cd Q[3][3]);
+
+// Trial orbitals of projector QMC: an orthonormal real basis P (N x n_occ,
+// row-major, site index (x1 L + x2) 3 + a) of the lowest n_occ eigenstates of
+// K + eps diag(+1, 0, -1 by sublattice), built from the momentum blocks
+// H(k) + eps diag(1, 0, -1): one Bloch state per self-conjugate momentum,
+// the real and imaginary parts of u(k) e^{i k.x} for each pair k, -k.
+// Returns 0, 1 (bad arguments) or 2 (open shell: the cut at n_occ falls
+// inside a degenerate level, gap < gap_min, or splits a pair k, -k).
+int trial_orbitals(int L, int n_occ, double eps, double t, double gap_min, std::vector<double> &P);
+
 }  // namespace dq

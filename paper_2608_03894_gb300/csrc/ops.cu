@@ -1,5 +1,6 @@
 // Stateless operator entry points of include/dqmc.h: one hot-path step on
 // caller-owned device memory.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <map>
@@ -202,6 +203,20 @@ dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, doub
   if (ws) cudaFreeAsync(ws, st);
   if (ex) cudaFreeAsync(ex, st);
   if (e != cudaSuccess) return cuda_fail(e, "gemm");
+  return DQMC_OK;
+} DQ_API_CATCH
+
+dqmc_status dqmc_op_trial_state(int L, int n_occ, double eps, double *P_out) try {
+  if (!supported_L(L)) return fail(DQMC_EINVAL, "unsupported L");
+  const int N = 3 * L * L;
+  if (n_occ < 1 || n_occ >= N) return fail(DQMC_EINVAL, "need 1 <= n_occ < N");
+  if (!P_out) return fail(DQMC_EINVAL, "P_out is NULL");
+  if (!std::isfinite(eps)) return fail(DQMC_EINVAL, "eps must be finite");
+  std::vector<double> P;
+  const int rc = trial_orbitals(L, n_occ, eps, 1.0, 1e-9, P);
+  if (rc == 2) return fail(DQMC_EINVAL, "open shell: the lowest n_occ states are not separated by a gap");
+  if (rc != 0) return fail(DQMC_EINVAL, "bad trial-state arguments");
+  std::copy(P.begin(), P.end(), P_out);
   return DQMC_OK;
 } DQ_API_CATCH
 

@@ -101,6 +101,17 @@ def measure(L, G, site_offsets=True):
     return dict(zip(("S_pair_G", "S_pair_dk", "phi2_G", "phi2_K", "density", "ekin"), out.tolist()))
 
 
+def trial_state(L, n_occ, eps=1e-4):
+    """Projector-QMC trial orbitals: N x n_occ orthonormal real basis of the
+    lowest n_occ eigenstates of K + eps diag(+1, 0, -1) (host numpy array)."""
+    import numpy as np
+    lib = _lib.load()
+    N = 3 * int(L) ** 2
+    P = np.zeros((N, int(n_occ)))
+    check(lib.dqmc_op_trial_state(int(L), int(n_occ), float(eps), P.ctypes.data_as(C.c_void_p)))
+    return P
+
+
 def gemm(A, B, C=None, alpha=1.0, beta=0.0, ta=False, tb=False, mode="f64"):
     """C = alpha op(A) op(B) + beta C (FP64 tensors). mode: "f64" (FP64 FMA),
     "df" (double-float on the FP32 units), "oz" (exact digit slices on the bf16

@@ -143,3 +143,42 @@ def test_load_rejects_damaged_checkpoints_before_any_device_work(lib, tmp_path, 
     assert lib.dqmc_load(h, str(path).encode()) == 1
     assert why in lib.dqmc_last_error().decode()
     lib.dqmc_destroy(h)
+
+
+@pytest.mark.parametrize("L,n_occ,eps", [(1, 1, 0.0), (2, 4, 0.0), (3, 9, 1e-4), (4, 16, 0.0), (4, 16, 1e-4),
+                                         (6, 36, 1e-4), (6, 13, 1e-4), (12, 144, 1e-4)])
+def test_trial_state_spans_the_oracle_trial_subspace(lib, L, n_occ, eps):
+    """dqmc_op_trial_state (host, momentum blocks) against the oracle's trial
+    state (dense eigendecomposition of K + eps diag(1, 0, -1)): orthonormal,
+    and the same occupied subspace (equal projectors)."""
+    import numpy as np
+    from oracle import model as omodel, pqmc
+    from paper_2608_03894_gb300 import ops
+    P = ops.trial_state(L, n_occ, eps)
+    ref = pqmc.trial_state(omodel.Model(L, 1.0, 0.1, -4.0, -1.0), n_occ, eps)
+    assert np.max(np.abs(P.T @ P - np.eye(n_occ))) < 1e-12
+    assert np.max(np.abs(P @ P.T - ref @ ref.T)) < 1e-9
+
+
+def test_trial_state_refuses_an_open_shell(lib):
+    import numpy as np
+    P = np.zeros((27, 9))
+    assert lib.dqmc_op_trial_state(3, 9, 0.0, P.ctypes.data_as(C.c_void_p)) == 1
+    assert "open shell" in lib.dqmc_last_error().decode()
+    assert lib.dqmc_op_trial_state(3, 0, 1e-4, P.ctypes.data_as(C.c_void_p)) == 1
+    assert lib.dqmc_op_trial_state(5, 3, 1e-4, P.ctypes.data_as(C.c_void_p)) == 1
+
+
+def test_trial_state_refuses_exactly_the_open_shells_the_oracle_refuses(lib):
+    import numpy as np
+    from oracle import model as omodel, pqmc
+    m = omodel.Model(6, 1.0, 0.1, -4.0, -1.0)
+    P = np.zeros((m.N, m.N))
+    for n in range(1, 41):
+        try:
+            pqmc.trial_state(m, n)
+            closed = True
+        except ValueError:
+            closed = False
+        rc = lib.dqmc_op_trial_state(6, n, 1e-4, P.ctypes.data_as(C.c_void_p))
+        assert (rc == 0) == closed, n
