@@ -29,6 +29,9 @@ attractive Hubbard model on the kagome lattice"):
   kinetic energy.
 * ``fock``     -- exact diagonalisation and Fock-space Trotter products on
   tiny tori (3 and 6 sites), and the brute-force sum over all HS fields.
+* ``lattices`` -- the other composite lattices of the appendix: the
+  triangular (1 x 1 blocks) and honeycomb (2 x 2 blocks) kinetic matrices
+  from their Kronecker forms and from geometry.
 * ``pqmc``     -- the projector (zero-temperature) variant of the paper
   (Sec. II): trial Slater determinant from the lowest N_occ eigenstates of
   K, G = I - R (L R)^{-1} L from orthonormal N x N_occ stacks, the same
@@ -41,4 +44,4 @@ convergence to exact diagonalisation, an exact-weight histogram of the Markov
 chain, and the Philox known-answer vectors.
 """
 
-from . import lattice, philox, model, green, measure, fock, dqmc, pqmc  # noqa: F401
+from . import lattice, lattices, philox, model, green, measure, fock, dqmc, pqmc  # noqa: F401
