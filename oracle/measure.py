@@ -14,6 +14,8 @@ Observables (all Sec. III / IV of the paper):
   density rho = (2/N) sum_x (1 - G_xx),
   kinetic energy per site (2/N) sum_ij K_ij (delta_ij - G_ji).
 Derived: R_Pair = 1 - S(Gamma + dk)/S(Gamma), P = sqrt(S(Gamma)/N), D(Q) = sqrt(<phi^+ phi>(Q)).
+Full-momentum maps (all Q of the mesh) evaluate the same two definitions at
+every Q.
 """
 
 import numpy as np
@@ -87,6 +89,29 @@ class Observables:
             "density": density(G),
             "ekin": kinetic_energy(G, self.K),
         }
+
+
+def pair_structure_factor_all(G, L1, L2=None, site_offsets=True):
+    """S_Pair(Q) at every mesh momentum Q = m1 b1 / L1 + m2 b2 / L2 (array
+    indexed [m1, m2]), each by the definition above."""
+    if L2 is None:
+        L2 = L1
+    S = np.zeros((L1, L2))
+    for m1 in range(L1):
+        for m2 in range(L2):
+            S[m1, m2] = pair_structure_factor(G, lattice.momentum_phase(m1, m2, L1, L2, site_offsets))
+    return S
+
+
+def cdw_correlator_all(G, L1, L2=None):
+    """<phi^+ phi>(Q) at every mesh momentum (array indexed [m1, m2])."""
+    if L2 is None:
+        L2 = L1
+    P = np.zeros((L1, L2))
+    for m1 in range(L1):
+        for m2 in range(L2):
+            P[m1, m2] = cdw_correlator(G, cdw_weights(L1, L2, m1, m2))
+    return P
 
 
 def derived(S_G, S_dk, phi2_G, phi2_K, N):
