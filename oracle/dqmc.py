@@ -40,8 +40,8 @@ class NumericError(RuntimeError):
 
 class Chain:
     def __init__(self, L, beta, dtau, U, mu, seed, n_stab=10, chain=0, t=1.0, L2=None,
-                 field=None, site_offsets=True):
-        self.model = Model(L, beta, dtau, U, mu, t=t, L2=L2)
+                 field=None, site_offsets=True, lattice="kagome"):
+        self.model = Model(L, beta, dtau, U, mu, t=t, L2=L2, lattice=lattice)
         m = self.model
         self.N, self.M = m.N, m.M
         self.seed, self.chain = int(seed), int(chain)
@@ -54,7 +54,7 @@ class Chain:
         self.field = (philox.initial_field(seed, chain, self.M, self.N) if field is None
                       else np.array(field, dtype=np.int8).reshape(self.M, self.N).copy())
         self.sweeps_done = 0
-        self.obs = measure.Observables(m.L1, m.L2, m.K, site_offsets)
+        self.obs = measure.Observables(m.L1, m.L2, m.K, site_offsets, lattice_name=lattice)
         self.samples = []          # one dict per measurement
         self.max_drift = 0.0
         self.accepted = 0

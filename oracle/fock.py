@@ -78,7 +78,8 @@ class Sectors:
                   if len(self.idx[n]) else np.zeros((0, 0)) for n in range(N + 1)]
         self.bits = [np.array([[(b >> i) & 1 for i in range(N)] for b in self.idx[n]], dtype=float)
                      for n in range(N + 1)]
-        self.obs = obs if obs is not None else measure.Observables(model.L1, model.L2, K)
+        self.obs = obs if obs is not None else measure.Observables(model.L1, model.L2, K,
+                                                                   lattice_name=getattr(model, "lattice", "kagome"))
 
     def _kin(self, nu, nd):
         ku, kd = self.k[nu], self.k[nd]
@@ -154,6 +155,8 @@ class Sectors:
         out = {k: v / Z for k, v in acc.items()}
         if self.obs.w_K is None:
             out["phi2_K"] = float("nan")
+        if self.obs.w_G is None:
+            out["phi2_G"] = float("nan")
         return out, Z, emin
 
     def trotter(self, M=None, with_green=False):
@@ -186,6 +189,8 @@ class Sectors:
         out = {k: v / Z for k, v in acc.items()}
         if self.obs.w_K is None:
             out["phi2_K"] = float("nan")
+        if self.obs.w_G is None:
+            out["phi2_G"] = float("nan")
         if with_green:
             out["G"] = np.eye(self.N) + Gacc / float(np.real(Z))
         return out, float(np.real(Z))
@@ -258,7 +263,8 @@ def brute_force_hs(model, obs=None, with_green=False):
     sum_s w_s). Weight w_s = prod e^{-lambda s} det(I + B_M ... B_1)^2.
     ``with_green`` adds the weighted average "G" of G = (I + B_M...B_1)^{-1}."""
     N, M = model.N, model.M
-    obs = obs if obs is not None else measure.Observables(model.L1, model.L2, model.K)
+    obs = obs if obs is not None else measure.Observables(model.L1, model.L2, model.K,
+                                                          lattice_name=getattr(model, "lattice", "kagome"))
     Wsum = 0.0
     acc = {k: 0.0 for k in measure.Observables.NAMES}
     Gacc = np.zeros((N, N))

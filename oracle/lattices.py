@@ -25,6 +25,24 @@ HON_A2 = np.array([-0.5, -np.sqrt(3.0) / 2.0])
 HON_TAU = np.array([[0.0, 0.0], [0.0, 1.0 / np.sqrt(3.0)]])
 
 SITES_PER_CELL = {"kagome": 3, "triangular": 1, "honeycomb": 2}
+# sublattice offsets in units of (A1, A2): honeycomb B = A + (0, 1/sqrt 3) = A - (A1 + A2) / 3
+TAU_FRAC = {"triangular": np.zeros((1, 2)), "honeycomb": np.array([[0.0, 0.0], [-1.0 / 3.0, -1.0 / 3.0]])}
+
+
+def momentum_phase(lattice, m1, m2, L1, L2=None, with_offsets=True):
+    """e^{i Q . r_i} for Q = m1 b1 / L1 + m2 b2 / L2 on the triangular or
+    honeycomb torus (site positions R + tau_a, or cell positions R)."""
+    if L2 is None:
+        L2 = L1
+    tau = TAU_FRAC[lattice]
+    n = len(tau)
+    ph = np.zeros(n * L1 * L2, dtype=complex)
+    for x1 in range(L1):
+        for x2 in range(L2):
+            for a in range(n):
+                f = np.array([x1, x2], dtype=float) + (tau[a] if with_offsets else 0.0)
+                ph[(x1 * L2 + x2) * n + a] = np.exp(2j * np.pi * (m1 * f[0] / L1 + m2 * f[1] / L2))
+    return ph
 
 
 def triangular_kinetic(L1, L2=None, t=1.0):

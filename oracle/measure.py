@@ -20,7 +20,7 @@ every Q.
 
 import numpy as np
 
-from . import lattice
+from . import lattice, lattices
 
 OMEGA = np.exp(2j * np.pi / 3.0)
 
@@ -68,23 +68,33 @@ class Observables:
 
     NAMES = ("S_pair_G", "S_pair_dk", "phi2_G", "phi2_K", "density", "ekin")
 
-    def __init__(self, L1, L2=None, K=None, site_offsets=True):
+    def __init__(self, L1, L2=None, K=None, site_offsets=True, lattice_name="kagome"):
         if L2 is None:
             L2 = L1
         self.L1, self.L2 = L1, L2
-        self.N = 3 * L1 * L2
-        self.K = K if K is not None else lattice.kinetic_matrix(L1, L2)
-        self.ph_G = lattice.momentum_phase(0, 0, L1, L2, site_offsets)
-        self.ph_dk = lattice.momentum_phase(1 % L1, 0, L1, L2, site_offsets)
-        self.w_G = cdw_weights(L1, L2, 0, 0)
-        kp = lattice.dirac_point(L1) if L1 == L2 else None
-        self.w_K = cdw_weights(L1, L2, kp[0], kp[1]) if kp is not None else None
+        self.lattice = lattice_name
+        if lattice_name == "kagome":
+            self.N = 3 * L1 * L2
+            self.K = K if K is not None else lattice.kinetic_matrix(L1, L2)
+            self.ph_G = lattice.momentum_phase(0, 0, L1, L2, site_offsets)
+            self.ph_dk = lattice.momentum_phase(1 % L1, 0, L1, L2, site_offsets)
+            self.w_G = cdw_weights(L1, L2, 0, 0)
+            kp = lattice.dirac_point(L1) if L1 == L2 else None
+            self.w_K = cdw_weights(L1, L2, kp[0], kp[1]) if kp is not None else None
+        else:
+            # other lattices: the pair structure factor, density and kinetic
+            # energy; the three-sublattice CDW order parameter is kagome's
+            self.N = lattices.SITES_PER_CELL[lattice_name] * L1 * L2
+            self.K = K if K is not None else lattices.kinetic(lattice_name, L1, L2)
+            self.ph_G = lattices.momentum_phase(lattice_name, 0, 0, L1, L2, site_offsets)
+            self.ph_dk = lattices.momentum_phase(lattice_name, 1 % L1, 0, L1, L2, site_offsets)
+            self.w_G = self.w_K = None
 
     def __call__(self, G):
         return {
             "S_pair_G": pair_structure_factor(G, self.ph_G),
             "S_pair_dk": pair_structure_factor(G, self.ph_dk),
-            "phi2_G": cdw_correlator(G, self.w_G),
+            "phi2_G": cdw_correlator(G, self.w_G) if self.w_G is not None else float("nan"),
             "phi2_K": cdw_correlator(G, self.w_K) if self.w_K is not None else float("nan"),
             "density": density(G),
             "ekin": kinetic_energy(G, self.K),

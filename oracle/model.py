@@ -16,13 +16,14 @@ Weight of a field s_{i,l}: prod_{i,l} e^{-lambda s_{il}} det(I + B_M ... B_1)^2,
 
 import numpy as np
 
-from . import lattice
+from . import lattice as lattice_mod
+from . import lattices
 
 
 class Model:
     """Parameters plus dense propagators for one kagome torus."""
 
-    def __init__(self, L, beta, dtau, U, mu, t=1.0, L2=None):
+    def __init__(self, L, beta, dtau, U, mu, t=1.0, L2=None, lattice="kagome"):
         if U > 0:
             raise ValueError("U > 0 (repulsive) has a sign problem in the charge channel; U <= 0 only")
         M = beta / dtau
@@ -32,9 +33,11 @@ class Model:
         self.L2 = int(L if L2 is None else L2)
         self.beta, self.dtau, self.U, self.mu, self.t = float(beta), float(dtau), float(U), float(mu), float(t)
         self.M = int(round(M))
-        self.N = 3 * self.L1 * self.L2
+        self.lattice = lattice
+        self.N = lattices.SITES_PER_CELL[lattice] * self.L1 * self.L2
         self.lam = float(np.arccosh(np.exp(self.dtau * abs(self.U) / 2.0)))
-        self.K = lattice.kinetic_matrix(self.L1, self.L2, self.t)
+        self.K = (lattice_mod.kinetic_matrix(self.L1, self.L2, self.t) if lattice == "kagome"
+                  else lattices.kinetic(lattice, self.L1, self.L2, self.t))
         w, V = np.linalg.eigh(self.K)
         self.eps, self.Vk = w, V
         self.expK = (V * np.exp(-self.dtau * w)) @ V.T      # e^{-dtau K}

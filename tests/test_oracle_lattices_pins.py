@@ -79,3 +79,67 @@ def test_planted_mistakes_are_caught():
     Y = np.kron(np.kron(I, I) + np.kron(I, K1) + np.kron(K1.T, I), delta)
     wrong = -(Y + Y.T)
     assert np.max(np.abs(wrong - lattices.kinetic_from_geometry("honeycomb", L, L))) > 0.5
+
+
+# ---------------------------------------------------------------- the chain on other lattices
+from oracle import dqmc, fock, green, measure, model  # noqa: E402
+
+_OBS = ("S_pair_G", "S_pair_dk", "density", "ekin")
+
+
+@pytest.mark.parametrize("lat,L1,L2,M", [("triangular", 2, 2, 1), ("triangular", 2, 2, 2),
+                                         ("triangular", 3, 1, 2), ("honeycomb", 2, 1, 1),
+                                         ("honeycomb", 1, 1, 3)])
+def test_hs_sum_equals_fock_trotter(lat, L1, L2, M):
+    """On the triangular and honeycomb tori the sum over all Ising fields of
+    prod e^{-lambda s} det(I + B_M ... B_1)^2 reproduces the Fock-space
+    Trotter trace, and its weighted Wick estimators the Fock-space averages."""
+    m = model.Model(L1, 0.1 * M, 0.1, -4.0, -0.5, L2=L2, lattice=lat)
+    bf, W = fock.brute_force_hs(m)
+    tr, Z = fock.Sectors(m).trotter()
+    assert abs(Z / (m.hs_constant() ** (m.N * m.M) * W) - 1.0) < 1e-12
+    for k in _OBS:
+        assert abs(bf[k] - tr[k]) < 1e-12 * max(1.0, abs(tr[k])), k
+    assert np.isnan(bf["phi2_G"]) and np.isnan(tr["phi2_G"])
+
+
+@pytest.mark.parametrize("lat", ["triangular", "honeycomb"])
+def test_u0_closed_form_other_lattices(lat):
+    m = model.Model(4, 8.0, 0.1, 0.0, -0.5, lattice=lat)
+    f = np.ones((m.M, m.N), dtype=np.int8)
+    for l in (0, 37, m.M):
+        assert np.max(np.abs(green.green_udv(m, f, l) - m.green_free())) < 1e-10
+
+
+def test_chain_samples_exact_field_distribution_honeycomb():
+    """Two sites (one honeycomb cell), M = 3: 64 fields; the field histogram
+    after each sweep matches the exact weights (chi^2)."""
+    import scipy.stats as sst
+    ch = dqmc.Chain(1, 0.3, 0.1, -4.0, -0.5, seed=7, n_stab=1, lattice="honeycomb")
+    probs = fock.field_weights(ch.model)
+    keys = list(probs.keys())
+    index = {k: n for n, k in enumerate(keys)}
+    counts = np.zeros(len(keys))
+    n = 6000
+    for _ in range(n):
+        ch.sweep()
+        counts[index[tuple(int(x) for x in ch.field.reshape(-1))]] += 1
+    p = np.array([probs[k] for k in keys])
+    expected = n * p
+    ok = expected > 5
+    chi2 = np.sum((counts[ok] - expected[ok]) ** 2 / expected[ok])
+    dof = ok.sum() - 1
+    assert chi2 < 2.0 * sst.chi2.ppf(0.999, dof), (chi2, dof)
+
+
+def test_observables_on_other_lattices_use_their_own_geometry():
+    """S_Pair phases follow the lattice's site positions: with offsets the
+    honeycomb Gamma + dk phase of sublattice B differs from the cell phase by
+    e^{i 2 pi (-1/3) / L}."""
+    L = 3
+    ph = lattices.momentum_phase("honeycomb", 1, 0, L, L, True)
+    pc = lattices.momentum_phase("honeycomb", 1, 0, L, L, False)
+    assert abs(ph[1] / pc[1] - np.exp(2j * np.pi * (-1.0 / 3.0) / L)) < 1e-14
+    assert abs(ph[0] - pc[0]) < 1e-14
+    obs = measure.Observables(L, lattice_name="triangular")
+    assert obs.N == L * L and obs.w_G is None
