@@ -49,20 +49,34 @@ class UDV:
         return (self.U * self.D[None, :]) @ self.T
 
 
-def right_chain(model, field, l):
-    """B(tau_l, 0) = B_l ... B_1 in UDV form (QR after every slice)."""
+def right_chain(model, field, l, every=1):
+    """B(tau_l, 0) = B_l ... B_1 in UDV form, a QR after every ``every`` slices
+    (the products of up to ``every`` slices are formed densely in between)."""
     u = UDV(model.N)
+    X = None
     for m in range(1, l + 1):
-        u.left_multiply(model.B(field[m - 1]))
+        B = model.B(field[m - 1])
+        X = B if X is None else B @ X
+        if m % every == 0 or m == l:
+            u.left_multiply(X)
+            X = None
     return u
 
 
-def left_chain(model, field, l):
+def left_chain(model, field, l, every=1):
     """B(beta, tau_l) = B_M ... B_{l+1}, kept as the UDV form of its transpose
-    B_{l+1}^T ... B_M^T, so that B(beta, tau_l) = T^T D U^T."""
+    B_{l+1}^T ... B_M^T, so that B(beta, tau_l) = T^T D U^T; a QR after every
+    ``every`` slices."""
     u = UDV(model.N)
+    X = None
+    cnt = 0
     for m in range(model.M, l, -1):
-        u.left_multiply(model.BT(field[m - 1]))
+        Bt = model.BT(field[m - 1])
+        X = Bt if X is None else Bt @ X
+        cnt += 1
+        if cnt % every == 0 or m == l + 1:
+            u.left_multiply(X)
+            X = None
     return u
 
 
@@ -80,9 +94,10 @@ def combine(right, left):
     return (Ulp / Dlmax[None, :]) @ Z
 
 
-def green_udv(model, field, l):
-    """Stabilised G(tau_l) for slice index l in 0..M."""
-    return combine(right_chain(model, field, l), left_chain(model, field, l))
+def green_udv(model, field, l, every=1):
+    """Stabilised G(tau_l) for slice index l in 0..M (a QR after every
+    ``every`` slices on both sides; 1 is the reference)."""
+    return combine(right_chain(model, field, l, every), left_chain(model, field, l, every))
 
 
 def product_chain(model, field, l):

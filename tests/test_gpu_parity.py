@@ -316,6 +316,23 @@ def test_replay_mixed_vs_fp64_full_size_L24(pkg):
     assert np.max(np.abs(out["mixed"] - out["fp64"])) < 1e-6
 
 
+def test_green_from_scratch_full_size_L24_against_oracle(pkg):
+    """At the headline size (L = 24, N = 1728, M = 240) the GPU's FP64
+    from-scratch G at the middle slice of a random field equals the oracle's
+    stabilised G (UDV chains with a QR every 8 slices, pinned against the
+    per-slice chain) on every entry."""
+    par = dict(L=24, beta=24.0, dtau=0.1, U=-4.0, mu=-1.0)
+    m = omodel.Model(**par)
+    f = random_field(m.M, m.N, seed=6)
+    with pkg.DQMC(**par, seed=1, k=32, n_stab=8, precision="fp64") as d:
+        d.field = f
+        G = d.green(120)
+    ref = ogreen.green_udv(m, f, 120, 8)
+    err = float(np.max(np.abs(G - ref)))
+    print(f"L=24 from-scratch G against the oracle: {err:.2e}")
+    assert err < 1e-9
+
+
 def test_batched_chains_equal_single_chains(pkg):
     """Chains of different sizes swept concurrently (own streams, one host
     thread each) make exactly the decisions they make alone."""

@@ -180,7 +180,18 @@ def test_udv_matches_direct_inversion_small_beta():
     m = model.Model(4, 1.0, 0.1, -4.0, -1.0)
     f = random_field(m.M, m.N, 3)
     for l in (0, 1, 5, 10):
-        assert np.max(np.abs(green.green_udv(m, f, l) - green.green_direct(m, f, l))) < 1e-12
+        for every in (1, 3):
+            assert np.max(np.abs(green.green_udv(m, f, l, every) - green.green_direct(m, f, l))) < 1e-12
+
+
+def test_udv_stabilisation_interval_does_not_change_g_large_beta():
+    """A QR after every 8 slices (dense 8-slice products in between) gives the
+    same G as a QR after every slice at beta = 24, where the unstabilised
+    product is far out of reach of FP64."""
+    m = model.Model(4, 24.0, 0.1, -4.0, -1.0)
+    f = random_field(m.M, m.N, 4)
+    for l in (0, 100, 240):
+        assert np.max(np.abs(green.green_udv(m, f, l, 8) - green.green_udv(m, f, l))) < 1e-10
 
 
 @pytest.mark.parametrize("L,beta", [(4, 24.0), (6, 36.0)])
