@@ -126,6 +126,10 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *   "site_offsets" 1 = S_Pair phases use site positions R + tau_a, 0 = cells;
  *   "bin"        measurements per bin (default 10);
  *   "drift_limit" hard limit on the refresh drift (default 1e-3 -> DQMC_ENUMERIC);
+ *   "pipeline"   1 (default): the next delayed-update block's Metropolis runs on
+ *                a second stream beside the current flush; 0: everything on the
+ *                context's stream, one kernel after another (the same decisions;
+ *                for profilers that serialise launches);
  *   "metro_reserve" shared memory in bytes (0..232448, default 204800) that the
  *                Metropolis block of the next delayed-update block claims while
  *                it runs beside the current flush, so that it has an SM to

@@ -214,6 +214,7 @@ struct dqmc_ctx {
   void *Abuf = nullptr;                       // N x K rank-m factor A (or its FP32 pairs)
   int df_flush = 1;   // mixed: rank-m flush as double-float product (else FP64)
   int df_prop = 1;    // mixed: FFT propagation in double-float arithmetic (else FP64)
+  int pipeline = 1;   // next block's Metropolis on the side stream beside the flush (0: one stream)
   int df_metro = 0;   // mixed: Metropolis recursions in double-float arithmetic (else FP64)
   int metro_reserve = 200 * 1024;  // shared memory the look-ahead Metropolis claims (own SM)
   int stab_gemm = 2;  // mixed: stabilisation GEMMs 0 FP64, 1 double-float, 2 tensor-core digit slices
@@ -553,20 +554,26 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
     CK(launch_amat<T>(K, fa, Gc[par], Gr[par], al, be, acc, c->Abuf, df, c->stream));
     if (fa.nkb > 0) {
       CK(launch_lookahead_g<T>(K, fa, G, c->Abuf, df, Gr[par], be, acc, c->gnext, c->stream));
-      CK(cudaEventRecord(c->ev_fork, c->stream));
-      CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+      // pipelined: the next block's Metropolis on the side stream, beside the
+      // flush; single-stream (pipeline = 0): before the flush on this stream
+      cudaStream_t ms = c->stream;
+      if (c->pipeline) {
+        CK(cudaEventRecord(c->ev_fork, c->stream));
+        CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        ms = c->side;
+      }
       MetroArgs mn = ma;
       mn.s0 = fa.ns0;
       mn.kb = fa.nkb;
       mn.ld_g = fa.nkb;
       CK(launch_metropolis(mn, c->gnext, false, s, forced ? forced + fa.ns0 : nullptr,
                            c->coef_a + (par ^ 1) * KK, c->coef_b + (par ^ 1) * KK, c->acc + (par ^ 1),
-                           c->status, c->total_acc, c->side, dfm, c->metro_reserve));
-      CK(cudaEventRecord(c->ev_join, c->side));
+                           c->status, c->total_acc, ms, dfm, c->pipeline ? c->metro_reserve : 0));
+      if (c->pipeline) CK(cudaEventRecord(c->ev_join, c->side));
     }
     CK(launch_flush_update<T>(K, fa, G, c->Abuf, Gr[par], be, acc, Gc[par ^ 1], Gr[par ^ 1], df,
                               c->stream));
-    if (fa.nkb > 0) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    if (fa.nkb > 0 && c->pipeline) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   }
   c->proposed += N;
   return DQMC_OK;
@@ -987,6 +994,8 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "stab_gemm must be 0, 1 or 2");
     c->stab_gemm = (int)v;
+  } else if (k == "pipeline") {
+    c->pipeline = v != 0.0;
   } else if (k == "drift_limit") {
     if (!(v > 0.0)) return fail(DQMC_EINVAL, "drift_limit must be positive");
     c->drift_limit = v;

@@ -520,3 +520,20 @@ def test_set_field_to_the_current_state_keeps_g(pkg):
         assert np.max(np.abs(G2 - ogreen.green_udv(m, f2, 0))) < 1e-10
         d.sweep(1)
         assert d.stats()["max_drift"] < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_single_stream_mode_is_bit_identical(pkg, prec):
+    """pipeline = 0 (the next block's Metropolis on the context's own stream,
+    before the flush) takes the same decisions as the two-stream pipeline and
+    gives the same G (up to the summation order of split-K GEMM partials,
+    which FP64 atomic adds do not fix)."""
+    par = dict(L=12, beta=2.0, dtau=0.1, U=-4.0, mu=-1.0)
+    out = {}
+    for pl in (1, 0):
+        with pkg.DQMC(**par, seed=4, k=32, n_stab=10, precision=prec) as d:
+            d.set_option("pipeline", pl)
+            d.sweep(2)
+            out[pl] = (d.field, d.running_green()[0])
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.max(np.abs(out[0][1] - out[1][1])) < 1e-10
