@@ -116,10 +116,24 @@ def workload(args):
     return w
 
 
+def parse_options(items):
+    """--option key=value (repeatable): library options set on the chain
+    before its first sweep, e.g. pipeline=0 for a single-stream sweep."""
+    out = {}
+    for it in items or []:
+        key, _, val = it.partition("=")
+        if not key or not val:
+            raise SystemExit(f"--option expects key=value, got {it!r}")
+        out[key] = float(val)
+    return out
+
+
 def config_dict(w, world):
     L = w["L"]
     M = int(round(w["beta"] / w["dtau"]))
-    return {
+    opts = parse_options(args_global.option)
+    extra = {"options": opts} if opts else {}
+    return {**extra, 
         "workload": f"{args_global.workload}: kagome L={L} (N={3 * L * L}), beta={w['beta']}, dtau={w['dtau']} "
                     f"(M={M}), U={w['U']}, mu={w['mu']}, k={w['k']}, n_stab={w['n_stab']}, "
                     f"precision={w['precision']}, one chain per GPU",
@@ -287,6 +301,8 @@ def run_ours(args, rank, world, local_rank):
     rp = replica(w, rank)
     d = pkg.DQMC(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], seed=rp["seed"], k=w["k"],
                  n_stab=w["n_stab"], precision=w["precision"], chain=rp["chain"])
+    for key, val in parse_options(args.option).items():
+        d.set_option(key, val)
     stream = torch.cuda.current_stream()
     d.sweep(args.warmup)
     launches0 = d.stats()["launches"]
@@ -450,6 +466,8 @@ def main():
     ap.add_argument("--workload", default="L24_mixed", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=("fp64", "mixed", "fp32"))
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--option", action="append", default=[],
+                    help="library option key=value for the chain (repeatable), e.g. pipeline=0")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--micro", default=None, choices=("prop", "gemm"),
