@@ -65,3 +65,18 @@ def test_reference_arm_under_torchrun_prints_once():
     import json
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_bench_options_are_parsed_and_recorded():
+    """`--option key=value` reaches the JSON line's config (reference arm,
+    one process, small workload); a malformed option stops the run."""
+    import json
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "L4_fp64",
+           "--steps", "1", "--warmup", "0", "--option", "pipeline=0", "--option", "metro_reserve=0"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][0])
+    assert d["config"]["options"] == {"pipeline": 0.0, "metro_reserve": 0.0}
+    bad = subprocess.run(cmd[:-2] + ["--option", "pipeline"], capture_output=True, text=True, timeout=600,
+                         cwd=ROOT)
+    assert bad.returncode != 0 and "key=value" in (bad.stderr + bad.stdout)
