@@ -154,9 +154,11 @@ def cpu_oracle_sample(w, budget_s=20.0):
     visits = max(1, min(64, M, int(budget_s / max(t1, 1e-3))))
     t, n, _ = odqmc.time_slice_visits(w["L"], w["beta"], w["dtau"], w["U"], w["mu"], w["seed"], visits,
                                       n_stab=w["n_stab"], with_refresh=False)
-    return {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle", "proposals": n, "seconds": t,
+            "refresh_excluded": True,
             "sample": f"{visits} up-pass slice visits at L={w['L']} (wrap + {3 * w['L'] ** 2} one-at-a-time "
-                      f"proposals each, numpy FP64 on {cores} host threads), UDV refresh excluded, {t:.1f} s"}
+                      f"proposals each, numpy FP64 on {cores} host threads), UDV refresh excluded "
+                      f"(so the rate overstates a whole oracle sweep), {t:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -170,14 +172,22 @@ def run_reference(args, rank, world):
         if i >= args.warmup:
             per_step.append(s)
         samples = s
-    value = statistics.mean(s["value"] for s in per_step)
+    # each step is a bounded sample (a few slice visits, not a whole sweep):
+    # value = proposals / s over the samples, ms_per_step = the samples' own time
+    props = sum(s["proposals"] for s in per_step)
+    secs = sum(s["seconds"] for s in per_step)
+    value = props / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * 2 * (3 * w["L"] ** 2) * int(round(w["beta"] / w["dtau"])) / value,
+        "ms_per_step": 1000.0 * secs / len(per_step),
+        "step_definition": "a bounded sample of up-pass slice visits of the workload (wrap + N "
+                           "one-at-a-time proposals each), UDV refresh excluded; not a whole sweep",
+        "extrapolated": False, "refresh_excluded": True,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (Philox-initialised Ising field)", "config": config_dict(w, world),
-        "cpu_baseline": {k: samples[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples["cores"], "kind": "oracle",
+                         "sample": samples["sample"], "refresh_excluded": True},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -434,6 +444,16 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu:
         cpu = soft(lambda: cpu_oracle_sample(w, budget_s=args.cpu_budget))
 
+    # ---- the metric's comparison: the plain FP64 GPU path (and plain FP32 as
+    # context) on the same workload, delay rank and refresh interval, timed the
+    # same way; the mixed arm's chain is released first
+    d_stats = st
+    d.close()
+    arms = {}
+    if rank == 0 and w["precision"] == "mixed" and args.compare_steps > 0:
+        for prec in ("fp64", "fp32"):
+            arms[prec] = soft(lambda p=prec: comparator_arm(w, p, rp, args.compare_steps))
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -443,17 +463,54 @@ def run_ours(args, rank, world, local_rank):
                       "fp32": "f32 + f64 stab"}[w["precision"]],
             "data": "synthetic (Philox-initialised Ising field, seed 1 + rank)",
             "config": config_dict(w, world),
-            "max_drift": st["max_drift"],
-            "acceptance": st["accepted"] / max(1, st["proposed"]),
+            "max_drift": d_stats["max_drift"],
+            "acceptance": d_stats["accepted"] / max(1, d_stats["proposed"]),
             "sweeps_per_s": args.steps * world / (ms / 1000.0),
             "phase_breakdown_ms": {f: round(v["ms"], 3) for f, v in fam.items()},
             "launches_before_timed": int(launches0),
             "roofline": roof, "fft_roofline": fft, "cpu_baseline": cpu, "e2e": e2e,
+            "fp64_arm": arms.get("fp64"), "fp32_arm": arms.get("fp32"),
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+        fa = arms.get("fp64")
+        if fa and "value" in fa and "error" not in fa:
+            line["fp64_value"] = fa["value"]
+            line["fp64_max_drift"] = fa["max_drift"]
+            line["speedup_vs_fp64"] = value / fa["value"]
+            line["mixed_drift_within_bar"] = bool(d_stats["max_drift"] <= 1e-6)
         print(json.dumps(line), flush=True)
-    d.close()
+
+
+def comparator_arm(w, prec, rp, steps):
+    """One more chain of the same workload (same seed, k, n_stab) in another
+    precision: one untimed warm-up sweep, then `steps` sweeps timed with CUDA
+    events on the library's stream. Returns its site-updates/s and drift."""
+    import torch
+
+    import paper_2608_03894_gb300 as pkg
+    L, N = w["L"], 3 * w["L"] ** 2
+    M = int(round(w["beta"] / w["dtau"]))
+    kw = {"drift_limit": 10.0} if prec == "fp32" else {}
+    with pkg.DQMC(L, w["beta"], w["dtau"], w["U"], w["mu"], seed=rp["seed"], k=w["k"],
+                  n_stab=w["n_stab"], precision=prec, chain=rp["chain"], **kw) as c:
+        for key, val in parse_options(args_global.option).items():
+            c.set_option(key, val)
+        stream = torch.cuda.current_stream()
+        c.sweep(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.sweep(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s = c.stats()
+    return {"precision": prec, "value": 2 * N * M * steps / (ms / 1000.0), "unit": UNIT,
+            "steps": steps, "warmup": 1, "ms_per_step": ms / steps, "max_drift": s["max_drift"],
+            "acceptance": s["accepted"] / max(1, s["proposed"]),
+            "note": {"fp64": "plain FP64 GPU path, same k and n_stab: the metric's denominator",
+                     "fp32": "plain FP32 propagation and flush (context: misses the |dG| <= 1e-6 bar)"}[prec]}
 
 
 def main():
@@ -469,6 +526,9 @@ def main():
     ap.add_argument("--option", action="append", default=[],
                     help="library option key=value for the chain (repeatable), e.g. pipeline=0")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--compare-steps", type=int, default=2,
+                    help="sweeps timed for the plain FP64 (and FP32) comparator arms of a mixed "
+                         "run; 0 skips them")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--micro", default=None, choices=("prop", "gemm"),
                     help="only a microbenchmark: the FFT propagation on a stacked operand larger "

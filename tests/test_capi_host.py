@@ -90,6 +90,19 @@ def test_null_arguments(lib):
     lib.dqmc_destroy(h)
 
 
+def test_field_values_other_than_plus_minus_one_are_refused_on_the_host(lib):
+    """dqmc_set_field / dqmc_replay check every value before any device work."""
+    st, h = _create(lib)
+    M, N = 20, 48
+    bad = (C.c_int8 * (M * N))(*([1] * (M * N - 1) + [2]))
+    G = (C.c_double * 1)()
+    assert lib.dqmc_set_field(h, bad) == 1
+    assert "+1 or -1" in lib.dqmc_last_error().decode()
+    assert lib.dqmc_replay(h, bad, 3, G) == 1
+    assert "+1 or -1" in lib.dqmc_last_error().decode()
+    lib.dqmc_destroy(h)
+
+
 def test_operator_argument_validation(lib):
     # rejected on the host before any launch
     assert lib.dqmc_op_propagate_f64(5, -0.1, 0, C.c_void_p(16), C.c_void_p(16), 1, 1, None, None, None, None) == 1
