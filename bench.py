@@ -246,11 +246,47 @@ def gemm_microbench(n, mode, reps=5):
     return {"n": n, "mode": mode, "ms": round(ms, 4), "TFLOP_s_fp64_equivalent": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 3)}
 
 
+def metro_microbench(L, k, df, reps=200):
+    """One delayed-update block alone (decisions + Woodbury coefficients) on a
+    G-like block of the L x L torus, then the rank-k flush of that block."""
+    import torch
+
+    import paper_2608_03894_gb300 as pkg
+    from dqmc_inputs import random_green_like
+    N = 3 * L * L
+    G = torch.as_tensor(random_green_like(N, 1), dtype=torch.float64, device="cuda")
+    s = torch.ones(N, dtype=torch.int8, device="cuda")
+    lam = 0.6538
+    g = G[:k, :k].contiguous()
+    Gcol, Grow = G[:, :k].contiguous(), G[:k, :].contiguous()
+    res = {}
+    for name in ("metropolis", "flush"):
+        for i in range(reps + 5):
+            if i == 5:
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+            if name == "metropolis":
+                al, be, cnt, _ = pkg.ops.metropolis_block(N, 0, k, g, s, lam, 1, 0, i, 1, df=df)
+            else:
+                pkg.ops.flush(N, 0, k, G, Gcol, Grow, al, be, cnt, mode="df" if df else "f64")
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_us"] = round(1000.0 * e0.elapsed_time(e1) / reps, 2)
+    return {"L": L, "k": k, "arith": "df" if df else "f64", **res}
+
+
 def run_micro(args):
     import torch
     torch.cuda.set_device(0)
     peaks, src = load_peaks()
     out = []
+    if args.micro == "metro":
+        for df in (False, True):
+            out.append(metro_microbench(args.micro_L, 32, df))
+            out.append(metro_microbench(args.micro_L, 64, df))
+        print(json.dumps({"micro": "metro", "results": out}), flush=True)
+        return
     if args.micro == "gemm":
         for mode in args.micro_prec.split(","):
             out.append(gemm_microbench(args.micro_n, mode))
@@ -530,10 +566,10 @@ def main():
                     help="sweeps timed for the plain FP64 (and FP32) comparator arms of a mixed "
                          "run; 0 skips them")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--micro", default=None, choices=("prop", "gemm"),
+    ap.add_argument("--micro", default=None, choices=("prop", "gemm", "metro"),
                     help="only a microbenchmark: the FFT propagation on a stacked operand larger "
                          "than L2 (prop; --micro-prec fp32,df,fp64), or the stabilisation GEMM "
-                         "(gemm; --micro-prec f64,df,oz, size --micro-n)")
+                         "(gemm; --micro-prec f64,df,oz,tc, size --micro-n)")
     ap.add_argument("--micro-n", type=int, default=1728)
     ap.add_argument("--micro-L", type=int, default=24)
     ap.add_argument("--micro-stack", type=int, default=64)

@@ -84,7 +84,7 @@ typedef struct {
   double ms_wrap, ms_update, ms_stab, ms_measure; /* device time per phase (timing >= 1) */
   /* device time and launch count per kernel family (timing = 2): 0 FFT
    * propagation, 1 Metropolis block, 2 rank-k flush, 3 stabilisation GEMMs,
-   * 4 QR panels, 5 measurement, 6 other small kernels, 7 operand splitting of
+   * 4 QR panels and Cholesky diagonal blocks, 5 measurement, 6 other small kernels, 7 operand splitting of
    * the emulated GEMMs, 8 delayed-update helpers (gathers, A/B factors,
    * look-ahead block), 9 stabilisation helpers (T factors, triangular
    * inverses, pivoting, scaling) */
@@ -113,11 +113,13 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *   "k"          delay rank (4, 8, 16, 32 or 64; default 32);
  *   "n_stab"     slices between UDV refreshes (default 10);
  *   "precision"  0 = plain FP64 (default);
- *                1 = mixed: FP64 data; propagation and flush in
- *                    double-float arithmetic (FP32 pairs, ~2^-47) on the
- *                    FP32 units; stabilisation products as exact digit slices
- *                    on the bf16 tensor cores; Metropolis, Householder panels
- *                    and triangular inverses in FP64;
+ *                1 = mixed: FP64 data; rank-m flush in double-float
+ *                    arithmetic (FP32 pairs, ~2^-47) on the FP32 units, FFT
+ *                    propagation in FP64 (see "df_prop"); stabilisation
+ *                    products as exact digit slices
+ *                    on the bf16 tensor cores; Metropolis decisions and
+ *                    Woodbury coefficients in double-float (see "df_metro");
+ *                    Householder panels and triangular inverses in FP64;
  *                2 = plain FP32 propagation and flush, which drifts by
  *                    1e-3..1e-1 per refresh interval (for comparison);
  *   "chain"      Philox chain id;
@@ -130,17 +132,19 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                a second stream beside the current flush; 0: everything on the
  *                context's stream, one kernel after another (the same decisions;
  *                for profilers that serialise launches);
- *   "metro_reserve" shared memory in bytes (0..232448, default 204800) that the
+ *   "metro_reserve" shared memory in bytes (0..229376, default 204800) that the
  *                Metropolis block of the next delayed-update block claims while
  *                it runs beside the current flush, so that it has an SM to
  *                itself; 0 = only what it needs;
  * mixed precision only (1 = double-float, 0 = native FP64 for that step):
  *   "df_flush"   rank-m flush as double-float products (default 1);
- *   "df_prop"    FFT propagation in double-float arithmetic (default 1);
- *   "df_metro"   Metropolis ratios and coefficient recursions in double-float
- *                arithmetic, the decision u < R on the FP64 value of R
- *                (default 0: no faster on the side stream, and its drift at
- *                L = 36 is 1.7e-6 against 4.8e-7 in FP64);
+ *   "df_prop"    FFT propagation in double-float arithmetic (default 0: the
+ *                propagation is ~4% of a sweep, and its rounding, applied to
+ *                the whole G every slice, dominated the double-float drift at
+ *                L = 36: 1.1e-6 against 4.5e-7 with FP64 propagation);
+ *   "df_metro"   Metropolis decisions, the tracked k x k block and the
+ *                Woodbury coefficients in double-float arithmetic (default 1;
+ *                0 = FP64, whose serial chain is ~8x slower on this part);
  *   "stab_gemm"  stabilisation GEMMs: 0 = FP64, 1 = double-float, 2 = exact
  *                7-bit digit slices on the bf16 tensor cores (default 2);
  *   "gemm_sites" 32-bit mask of the stabilisation GEMM call sites that use the
@@ -149,9 +153,20 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                double-float GEMM instead (default 0). Site bits: 0 QR trailing
  *                update, 1 explicit Q, 2 T update, 3 U_r^T U_l, 4 T_r T_l^T,
  *                5 QR of the scale-separated matrix, 6 Q^T B, 7 triangular
- *                solve, 8 final product.
+ *                solve, 8 final product, 9 CholeskyQR2 (Gram matrices,
+ *                Cholesky recursion, Q and R products).
+ *   "stab_qr"    orthogonal-triangular factorisation of the stabilisation:
+ *                0 = Householder QR (panels on one thread-block cluster),
+ *                1 = CholeskyQR2 for the stack products and shifted
+ *                CholeskyQR3 for the scale-separated matrix (all but 64 x 64
+ *                diagonal blocks as GEMMs; slower than Householder with the
+ *                present GEMMs, and its Gram matrix loses definiteness on
+ *                the L = 36 stacks), 0 (default) = Householder, -1 =
+ *                CholeskyQR in mixed precision only. dqmc_green always uses
+ *                Householder QR. A non-positive Cholesky pivot makes
+ *                dqmc_sweep return DQMC_ENUMERIC.
  * "k", "n_stab", "precision", "chain", "df_flush", "df_prop", "df_metro",
- * "stab_gemm" and "gemm_df_sites" are accepted only before the first sweep;
+ * "stab_gemm", "stab_qr" and "gemm_df_sites" are accepted only before the first sweep;
  * later they return DQMC_ESTATE. */
 dqmc_status dqmc_set_option(dqmc_ctx *ctx, const char *key, double value);
 
@@ -281,13 +296,25 @@ dqmc_status dqmc_op_propagate_f32(int L, double scale, int side, const float *X,
  * rows 0..m-1 hold the coefficient vectors of the accepted flips in order, the
  * other rows zero, such that the m sequential Sherman-Morrison updates equal
  *   G' = G - (G[:,S] alpha^T) (beta (E_S - G[S,:]))
- * with E_S the kb x N selector of S. Non-positive or non-finite ratios set
- * *status = 1 and stop. forced != NULL (kb bytes) replaces the decision. */
+ * with E_S the kb x N selector of S: alpha^T beta is the Woodbury matrix
+ * Gamma = (Delta^{-1} + I - G[P,P])^{-1} of the accepted sites P (row r of
+ * beta selects the r-th accepted site, row r of alpha is column r of Gamma).
+ * Non-positive or non-finite ratios set *status = 1 and stop. forced != NULL
+ * (kb bytes) replaces the decision. */
 dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, int ld_g,
                                      int8_t *s, double lambda, uint64_t seed, uint32_t chain,
                                      uint32_t sweep_pass, int slice1, const uint8_t *forced,
                                      double *alpha, double *beta, int *accept_count, int *status,
                                      void *stream);
+/* The same block with the decision arithmetic (the tracked k x k block, the
+ * ratios) and the Woodbury coefficients in double-float arithmetic (FP32
+ * pairs, ~2^-47) on the FP32 units: the mixed precision mode's Metropolis.
+ * Same arguments, outputs and errors as dqmc_op_metropolis_block. */
+dqmc_status dqmc_op_metropolis_block_df(int N, int site0, int kb, const double *g, int ld_g,
+                                        int8_t *s, double lambda, uint64_t seed, uint32_t chain,
+                                        uint32_t sweep_pass, int slice1, const uint8_t *forced,
+                                        double *alpha, double *beta, int *accept_count, int *status,
+                                        void *stream);
 
 /* Rank-m flush of one block: G <- G - (Gcol alpha^T)(beta (E_S - Grow)), with
  * Gcol = G[:,S] (N x kb, ld kb) and Grow = G[S,:] (kb x N, ld N) taken before
@@ -330,7 +357,9 @@ dqmc_status dqmc_op_flush_f64_noalloc(int N, int site0, int kb, double *G, const
  * device), op = transpose when ta / tb. mode 0: FP64 FMA; 1: FP64-accurate
  * double-float product on the FP32 units; 2: FP64-accurate product from exact
  * 7-bit digit slices on the bf16 tensor cores (Ozaki-style error-free
- * splitting; the stabilisation of the mixed precision mode uses it).
+ * splitting; the stabilisation of the mixed precision mode uses it), warp-level
+ * mma.sync; 3: the same digit slices on tcgen05 with tensor-memory
+ * accumulators.
  * Modes 1-2 allocate their operand workspace on the stream. */
 dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, double alpha,
                              const double *A, int lda, const double *B, int ldb, double beta,

@@ -65,6 +65,7 @@ SIGNATURES = {
     "dqmc_op_propagate_f32": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_propagate_df": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_metropolis_block": (i32, [i32, i32, i32, vp, i32, vp, f64, u64, u32, u32, i32, vp, vp, vp, vp, vp, vp]),
+    "dqmc_op_metropolis_block_df": (i32, [i32, i32, i32, vp, i32, vp, f64, u64, u32, u32, i32, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_f64": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_df": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_f32": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256)
     dfgemm_kernel(int M, int N, int K, double alpha, const float2 *__restrict__ A,
                   const float2 *__restrict__ B, double beta, double *__restrict__ C, int ldc,
                   const double *__restrict__ rs, const double *__restrict__ cs, int klen,
-                  int atomic) {
+                  double *__restrict__ part) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ float2 As[BK][BM + 1];
   __shared__ float2 Bs[BK][BN + 1];
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(256)
       const double acc = (double)sh[i][j] + (double)sl[i][j];
       const double v = alpha * r * acc * (cs ? cs[gn] : 1.0);
       double *cp = C + (size_t)gm * ldc + gn;
-      if (atomic)
-        atomicAdd(cp, v);
+      if (part)
+        part[((size_t)blockIdx.z * M + gm) * N + gn] = v;
       else
         *cp = (beta != 0.0) ? v + beta * (*cp) : v;
     }
@@ -178,24 +178,26 @@ cudaError_t dfgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
   int klen = (K + splitk - 1) / splitk;
   klen = ((klen + 15) / 16) * 16;
   splitk = (K + klen - 1) / klen;
-  const int atomic = splitk > 1;
-  if (atomic) {
-    cudaError_t e = scale_matrix(C, M, N, ldc, beta, st);
-    if (e != cudaSuccess) return e;
+  double *part = splitk_partials(splitk, M, N);
+  if (splitk > 1 && !part) {
+    splitk = 1;
+    klen = ((K + 15) / 16) * 16;
   }
   dim3 grid((N + 63) / 64, (M + 63) / 64, splitk);
   DQ_KSCOPE(KF_GEMM, st);
   add_work(KF_GEMM, 2.0 * M * (double)N * K,
            8.0 * ((double)M * K + (double)K * N + (beta != 0.0 ? 2.0 : 1.0) * (double)M * N));
   if (!ta && !tb)
-    dfgemm_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, As, Bs, beta, C, ldc, rs, cs, klen, atomic);
+    dfgemm_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, As, Bs, beta, C, ldc, rs, cs, klen, part);
   else if (ta && !tb)
-    dfgemm_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, As, Bs, beta, C, ldc, rs, cs, klen, atomic);
+    dfgemm_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, As, Bs, beta, C, ldc, rs, cs, klen, part);
   else if (!ta && tb)
-    dfgemm_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, As, Bs, beta, C, ldc, rs, cs, klen, atomic);
+    dfgemm_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, As, Bs, beta, C, ldc, rs, cs, klen, part);
   else
-    dfgemm_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, As, Bs, beta, C, ldc, rs, cs, klen, atomic);
-  return cudaGetLastError();
+    dfgemm_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, As, Bs, beta, C, ldc, rs, cs, klen, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !part) return e;
+  return splitk_reduce(part, splitk, M, N, beta, C, ldc, st);
 }
 
 }  // namespace dq

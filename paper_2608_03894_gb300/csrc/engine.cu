@@ -213,11 +213,13 @@ struct dqmc_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void *Abuf = nullptr;                       // N x K rank-m factor A (or its FP32 pairs)
   int df_flush = 1;   // mixed: rank-m flush as double-float product (else FP64)
-  int df_prop = 1;    // mixed: FFT propagation in double-float arithmetic (else FP64)
+  int df_prop = 0;    // mixed: FFT propagation in double-float arithmetic (default: FP64)
   int pipeline = 1;   // next block's Metropolis on the side stream beside the flush (0: one stream)
-  int df_metro = 0;   // mixed: Metropolis recursions in double-float arithmetic (else FP64)
+  int df_metro = 1;   // mixed: Metropolis decisions and Woodbury coefficients in double-float
   int metro_reserve = 200 * 1024;  // shared memory the look-ahead Metropolis claims (own SM)
   int stab_gemm = 2;  // mixed: stabilisation GEMMs 0 FP64, 1 double-float, 2 tensor-core digit slices
+  int stab_qr = 0;    // 0 Householder QR, 1 CholeskyQR2, -1 = CholeskyQR2 in mixed precision only
+  bool cholqr = false;  // the sweep's stabilisation uses CholeskyQR2 (resolved at allocation)
   unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
   unsigned gemm_df_sites = 0u;        // mixed: of those, the sites that use double-float products
   void *ozws = nullptr;  // digit-slice workspace
@@ -232,9 +234,11 @@ struct dqmc_ctx {
   double *ph_pc = nullptr, *ph_ps = nullptr, *ph_wgc = nullptr, *ph_wgs = nullptr,
          *ph_wkc = nullptr, *ph_wks = nullptr;
   int *nbr = nullptr;
+  double *skws = nullptr;  // split-K partial products of the stabilisation GEMMs
   float2 *dfws = nullptr;  // double-float GEMM workspace (mixed precision)
   size_t dfws_elems = 0;
   bool haveK = false;
+  bool reference_chain = false;  // dqmc_green: Householder QR after every slice, whatever the mode
   // host statistics
   long sweeps = 0, proposed = 0, accepted = 0;
   double max_drift = 0.0, last_drift = 0.0;
@@ -332,6 +336,8 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
   DQ_CHECK(ctx_alloc_n(c, &c->evi64, (size_t)N));
   DQ_CHECK(ctx_alloc_n(c, &c->ev32, (size_t)N));
   DQ_CHECK(ctx_alloc_n(c, &c->evi32, (size_t)N));
+  DQ_CHECK(ctx_alloc_n(c, &c->skws, splitk_ws_doubles()));
+  c->cholqr = c->stab_qr == 1 || (c->stab_qr < 0 && c->precision == 1);
   if (c->precision == 1 && (c->stab_gemm == 1 || c->gemm_df_sites != 0)) {
     // split operands of the double-float GEMMs: at most M*K + K*N = 2 N^2 pairs
     c->dfws_elems = 2 * NN;
@@ -517,8 +523,8 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
   T *Gc[2] = {static_cast<T *>(c->Gcol[0]), static_cast<T *>(c->Gcol[1])};
   T *Gr[2] = {static_cast<T *>(c->Grow[0]), static_cast<T *>(c->Grow[1])};
   const bool df = (c->precision == 1 && c->df_flush);
-  const bool dfm = (c->precision == 1 && c->df_metro);
   CK(launch_gather<T>(N, 0, std::min(K, N), K, G, Gc[0], Gr[0], c->stream));
+  const bool dfm = (c->precision == 1 && c->df_metro);
   MetroArgs ma;
   ma.N = N;
   ma.K = K;
@@ -605,6 +611,16 @@ dqmc_status udv_advance(dqmc_ctx *c, const UDVd &src, UDVd &dst, const std::vect
   CK(column_norms_scaled(c->X, N, src.D, c->norms, c->stream));
   CK(argsort_desc(c->norms, N, c->perm, c->stream));
   CK(permute_udv(c->X, src.D, src.T, c->perm, N, c->Xp, c->Dp, c->Tp, c->stream));
+  if (c->cholqr && !c->reference_chain) {
+    // Xp = U R by CholeskyQR2: U to dst.U, R to Mm (scratch X, Z, Bm and the
+    // QR workspace's V), then R'' = diag(D_new)^{-1} R diag(Dp), T_new = R'' P^T T_old
+    set_gemm_site(GS_CHOLQR);
+    CK(cholqr2(c->Xp, N, dst.U, c->Mm, c->X, c->Z, c->Bm, c->qr.V, c->status + 1, c->stream));
+    CK(udv_diag_and_scale(c->Mm, N, c->Dp, dst.D, c->stream));
+    set_gemm_site(GS_T_UPDATE);
+    CK(dgemm(false, false, N, N, N, 1.0, c->Mm, N, c->Tp, N, 0.0, dst.T, N, nullptr, nullptr, c->stream));
+    return DQMC_OK;
+  }
   set_gemm_site(GS_QR_UPDATE);
   CK(qr_factor(c->Xp, N, c->qr, c->stream));
   set_gemm_site(GS_FORM_Q);
@@ -635,12 +651,37 @@ dqmc_status combine(dqmc_ctx *c, const UDVd &r, const UDVd &lf, double *Gout) {
   set_gemm_site(GS_TT);
   CK(dgemm(false, true, N, N, N, 1.0, r.T, N, lf.T, N, 1.0, c->Mm, N, c->drmin, c->dlmin, c->stream));
   CK(transpose_scale(r.U, N, c->Bm, N, c->drmax_inv, c->stream));
-  set_gemm_site(GS_QRM);
-  CK(qr_factor(c->Mm, N, c->qr, c->stream));
-  set_gemm_site(GS_APPLY_QT);
-  CK(qr_apply_qt(c->Bm, N, N, N, c->qr, c->stream));
-  set_gemm_site(GS_TRSM);
-  CK(qr_solve_r(c->Mm, N, c->Bm, c->Z, N, c->qr, c->stream));
+  if (c->cholqr && !c->reference_chain) {
+    // M^{-1} B by shifted CholeskyQR3 of M (Fukaya, Kannan, Nakatsukasa,
+    // Yamamoto, Yanagisawa 2020): a first pass on M^T M + s I, s = 11 (n^2 +
+    // n (n + 1)) u tr(M^T M), keeps the Cholesky factorisation defined up to
+    // cond(M) ~ 1/u (the scale-separated matrix of a random field reaches
+    // 1e7 - 1e8 here), then CholeskyQR2 of the result: M = Q R, R = R2 R1 R0,
+    // Z = R0^{-1} R1^{-1} R2^{-1} Q^T B.
+    const double shift = 11.0 * (2.0 * (double)N * N + N) * 0x1p-53;
+    set_gemm_site(GS_CHOLQR);
+    CK(dgemm(true, false, N, N, N, 1.0, c->Mm, N, c->Mm, N, 0.0, c->Z, N, nullptr, nullptr, c->stream));
+    CK(shift_diag(c->Z, N, N, shift, c->stream));
+    CK(chol_inv(c->Z, N, c->X, N, c->Xp, N, N, c->status + 1, c->stream));               // R0^{-1} -> X
+    CK(dgemm(false, false, N, N, N, 1.0, c->Mm, N, c->X, N, 0.0, c->Tp, N, nullptr, nullptr, c->stream));   // Q0
+    CK(dgemm(true, false, N, N, N, 1.0, c->Tp, N, c->Tp, N, 0.0, c->Z, N, nullptr, nullptr, c->stream));
+    CK(chol_inv(c->Z, N, c->Xp, N, c->Mm, N, N, c->status + 1, c->stream));              // R1^{-1} -> Xp
+    CK(dgemm(false, false, N, N, N, 1.0, c->Tp, N, c->Xp, N, 0.0, c->Mm, N, nullptr, nullptr, c->stream));  // Q1
+    CK(dgemm(false, false, N, N, N, 1.0, c->X, N, c->Xp, N, 0.0, c->Tp, N, nullptr, nullptr, c->stream));   // R0^{-1} R1^{-1}
+    CK(dgemm(true, false, N, N, N, 1.0, c->Mm, N, c->Mm, N, 0.0, c->Z, N, nullptr, nullptr, c->stream));
+    CK(chol_inv(c->Z, N, c->Xp, N, c->X, N, N, c->status + 1, c->stream));               // R2^{-1} -> Xp
+    CK(dgemm(false, false, N, N, N, 1.0, c->Mm, N, c->Xp, N, 0.0, c->X, N, nullptr, nullptr, c->stream));   // Q
+    CK(dgemm(false, false, N, N, N, 1.0, c->Tp, N, c->Xp, N, 0.0, c->Mm, N, nullptr, nullptr, c->stream));  // R^{-1}
+    CK(dgemm(true, false, N, N, N, 1.0, c->X, N, c->Bm, N, 0.0, c->Tp, N, nullptr, nullptr, c->stream));    // Q^T B
+    CK(dgemm(false, false, N, N, N, 1.0, c->Mm, N, c->Tp, N, 0.0, c->Z, N, nullptr, nullptr, c->stream));
+  } else {
+    set_gemm_site(GS_QRM);
+    CK(qr_factor(c->Mm, N, c->qr, c->stream));
+    set_gemm_site(GS_APPLY_QT);
+    CK(qr_apply_qt(c->Bm, N, N, N, c->qr, c->stream));
+    set_gemm_site(GS_TRSM);
+    CK(qr_solve_r(c->Mm, N, c->Bm, c->Z, N, c->qr, c->stream));
+  }
   CK(scale_rows_cols(c->Z, N, N, c->dlmax_inv, nullptr, c->stream));
   set_gemm_site(GS_FINAL);
   CK(dgemm(false, false, N, N, N, 1.0, lf.U, N, c->Z, N, 0.0, Gout, N, nullptr, nullptr, c->stream));
@@ -686,6 +727,7 @@ __global__ void drift_max_kernel(const double *d, double *mx) {
 // double-float products on the FP32 units.
 struct GemmModeScope {
   explicit GemmModeScope(dqmc_ctx *c) {
+    set_splitk_workspace(c->skws, splitk_ws_doubles());
     if (c->precision != 1) return;
     if (c->stab_gemm == 1 && c->dfws) {
       set_df_workspace(c->dfws, c->dfws_elems);
@@ -702,6 +744,7 @@ struct GemmModeScope {
     set_gemm_df_site_mask(c->stab_gemm == 2 ? c->gemm_df_sites : 0u);
   }
   ~GemmModeScope() {
+    set_splitk_workspace(nullptr, 0);
     set_gemm_df(false);
     set_gemm_oz(false);
     set_gemm_df_site_mask(0u);
@@ -900,6 +943,9 @@ dqmc_status read_status(dqmc_ctx *c) {
   c->last_drift = dm;
   c->max_drift = std::max(c->max_drift, dm);
   if (st[0] != 0) return fail(DQMC_ENUMERIC, "non-positive or non-finite acceptance ratio");
+  if (st[1] != 0)
+    return fail(DQMC_ENUMERIC, "non-positive pivot in the Cholesky factorisation of the CholeskyQR2 "
+                               "stabilisation (set stab_qr = 0 for Householder QR)");
   if (!(dm <= c->drift_limit)) {
     char buf[160];
     std::snprintf(buf, sizeof(buf), "stabilisation drift %.3e above the limit %.3e", dm, c->drift_limit);
@@ -975,7 +1021,7 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     c->df_flush = v != 0.0;
   } else if (k == "metro_reserve") {
-    if (v < 0 || v > 227 * 1024) return fail(DQMC_EINVAL, "metro_reserve must be in [0, 232448] bytes");
+    if (v < 0 || v > 224 * 1024) return fail(DQMC_EINVAL, "metro_reserve must be in [0, 229376] bytes");
     c->metro_reserve = (int)v;
   } else if (k == "df_metro") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
@@ -994,6 +1040,10 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "stab_gemm must be 0, 1 or 2");
     c->stab_gemm = (int)v;
+  } else if (k == "stab_qr") {
+    if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
+    if (v != 0.0 && v != 1.0 && v != -1.0) return fail(DQMC_EINVAL, "stab_qr must be -1 (auto), 0 or 1");
+    c->stab_qr = (int)v;
   } else if (k == "pipeline") {
     c->pipeline = v != 0.0;
   } else if (k == "drift_limit") {
@@ -1055,6 +1105,15 @@ dqmc_status dqmc_green(dqmc_ctx *c, int slice, double *G_out) try {
   if (slice < 0 || slice > c->M) return fail(DQMC_EINVAL, "slice out of range");
   PhaseTimer tm(c);
   DQ_CHECK(ensure_ready(c));
+  struct SplitKScope {
+    explicit SplitKScope(dqmc_ctx *cc) { set_splitk_workspace(cc->skws, splitk_ws_doubles()); }
+    ~SplitKScope() { set_splitk_workspace(nullptr, 0); }
+  } sk(c);
+  struct RefScope {
+    dqmc_ctx *cc;
+    explicit RefScope(dqmc_ctx *x) : cc(x) { cc->reference_chain = true; }
+    ~RefScope() { cc->reference_chain = false; }
+  } ref(c);
   // right chain B(slice, 0) in tmpA, left chain B(beta, slice)^T in tmpB, QR every n_stab slices
   DQ_CHECK(udv_identity(c, c->tmpA));
   // reference-quality chains: a pivoted QR after every slice

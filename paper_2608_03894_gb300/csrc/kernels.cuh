@@ -36,9 +36,10 @@ struct MetroArgs {
   uint32_t c2, c3;       // counter words 2 (2*sweep + pass) and 3 (chain | domain << 24)
   int slice0;            // counter word 1 (0-based slice)
 };
-// df: the recursions in double-float arithmetic (mixed precision), else FP64.
-// reserve_smem: shared memory to claim (bytes, <= 227 KB) so that the block
-// has its SM to itself while another kernel runs concurrently; 0 = its need.
+// Decisions and Woodbury coefficients of one block (see update.cu), in FP64
+// or (df) double-float arithmetic. reserve_smem: shared memory to claim
+// (bytes, <= 224 KB) so that the block has its SM to itself while another
+// kernel runs concurrently; 0 = its need.
 cudaError_t launch_metropolis(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
                               const uint8_t *forced, double *alpha, double *beta, int *accept_count,
                               int *status, unsigned long long *total, cudaStream_t st,

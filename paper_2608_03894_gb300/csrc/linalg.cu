@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256)
     dgemm_kernel(int M, int N, int K, double alpha, const double *__restrict__ A, int lda,
                  const double *__restrict__ B, int ldb, double beta, double *__restrict__ C,
                  int ldc, const double *__restrict__ rs, const double *__restrict__ cs, int klen,
-                 int atomic) {
+                 double *__restrict__ part) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(256)
       if (gn >= N) continue;
       const double v = alpha * r * acc[i][j] * (cs ? cs[gn] : 1.0);
       double *cp = C + (size_t)gm * ldc + gn;
-      if (atomic)
-        atomicAdd(cp, v);
+      if (part)
+        part[((size_t)blockIdx.z * M + gm) * N + gn] = v;
       else
         *cp = (beta != 0.0) ? v + beta * (*cp) : v;
     }
@@ -116,11 +116,52 @@ __global__ void scale_matrix_kernel(double *C, int M, int N, int ldc, double bet
   }
 }
 
-static int grid_for(long work, int per = 256) {
+static int grid_for(long work, int per) {
   long g = (work + per - 1) / per;
   if (g > 8192) g = 8192;
   if (g < 1) g = 1;
   return (int)g;
+}
+
+// ---------------------------------------------------------------------- split K
+static thread_local double *t_skws = nullptr;
+static thread_local size_t t_skws_n = 0;
+
+void set_splitk_workspace(double *ws, size_t n) {
+  t_skws = ws;
+  t_skws_n = ws ? n : 0;
+}
+
+// The GEMMs split K only while their 64 x 64 tiles number fewer than 304, and
+// then into at most ceil(304 / tiles) splits: splits * M * N < 608 * 64 * 64.
+size_t splitk_ws_doubles() { return (size_t)608 * 64 * 64; }
+
+double *splitk_partials(int splits, int M, int N) {
+  if (splits <= 1) return nullptr;
+  const size_t need = (size_t)splits * M * N;
+  return (t_skws && need <= t_skws_n) ? t_skws : nullptr;
+}
+
+__global__ void splitk_reduce_kernel(const double *__restrict__ part, int splits, int M, int N,
+                                     double beta, double *__restrict__ C, int ldc) {
+  const long total = (long)M * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * total + e];
+    const int i = (int)(e / N), j = (int)(e % N);
+    double *cp = C + (size_t)i * ldc + j;
+    *cp = (beta != 0.0) ? s + beta * (*cp) : s;
+  }
+}
+
+static int grid_for(long work, int per = 256);
+
+cudaError_t splitk_reduce(const double *part, int splits, int M, int N, double beta, double *C,
+                          int ldc, cudaStream_t st) {
+  DQ_KSCOPE(KF_STABAUX, st);
+  splitk_reduce_kernel<<<grid_for((long)M * N), 256, 0, st>>>(part, splits, M, N, beta, C, ldc);
+  return cudaGetLastError();
 }
 
 static thread_local int t_site = 0;
@@ -173,24 +214,26 @@ cudaError_t dgemm_fp64(bool ta, bool tb, int M, int N, int K, double alpha, cons
   int klen = (K + splitk - 1) / splitk;
   klen = ((klen + 15) / 16) * 16;
   splitk = (K + klen - 1) / klen;
-  const int atomic = splitk > 1;
-  if (atomic) {
-    DQ_KSCOPE(KF_STABAUX, st);
-    scale_matrix_kernel<<<grid_for((long)M * N), 256, 0, st>>>(C, M, N, ldc, beta);
+  double *part = splitk_partials(splitk, M, N);
+  if (splitk > 1 && !part) {
+    splitk = 1;
+    klen = ((K + 15) / 16) * 16;
   }
   dim3 grid((N + 63) / 64, (M + 63) / 64, splitk);
   DQ_KSCOPE(KF_GEMM, st);
   add_work(KF_GEMM, 2.0 * M * (double)N * K,
            8.0 * ((double)M * K + (double)K * N + (beta != 0.0 ? 2.0 : 1.0) * (double)M * N));
   if (!ta && !tb)
-    dgemm_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
+    dgemm_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, part);
   else if (ta && !tb)
-    dgemm_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
+    dgemm_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, part);
   else if (!ta && tb)
-    dgemm_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
+    dgemm_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, part);
   else
-    dgemm_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, atomic);
-  return cudaGetLastError();
+    dgemm_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rs, cs, klen, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !part) return e;
+  return splitk_reduce(part, splitk, M, N, beta, C, ldc, st);
 }
 
 // ====================================================================== QR panel

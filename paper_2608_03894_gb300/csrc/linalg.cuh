@@ -7,8 +7,10 @@ namespace dq {
 
 // C = alpha diag(rs) op(A) op(B) diag(cs) + beta C; rs/cs may be NULL.
 // A is M x K (lda) or, transposed, K x M; B is K x N (ldb) or N x K.
-// splitk > 1 splits K over CTAs and accumulates with atomics (C is first
-// scaled by beta in a separate pass).
+// splitk > 1 splits K over CTAs: each split writes its partial product to the
+// calling thread's split-K workspace and one more kernel sums the splits in a
+// fixed order (results do not depend on CTA scheduling). Without a workspace
+// large enough for splits * M * N doubles the GEMM runs unsplit.
 // While set_gemm_df(true) is in effect for the calling thread (and a
 // workspace is bound), dgemm runs as dfgemm: FP64 in and out, FP64-accurate
 // products computed on the FP32 units from (hi, lo) FP32 pairs.
@@ -36,6 +38,12 @@ size_t oz_workspace_bytes(int M, int N, int K);
 void set_oz_workspace(void *ws, size_t bytes, int *exps, size_t nexp);  // exps: >= M + N ints
 void set_gemm_oz(bool on);
 bool gemm_oz();
+// While set_gemm_oz_tc(true) is in effect for the calling thread, the
+// digit-slice products run on tcgen05 (tensor memory accumulators) instead of
+// the warp-level mma.sync kernel. oz_tc_timed_out: whether a bounded wait of
+// that kernel gave up since the library was loaded (synchronises the stream).
+void set_gemm_oz_tc(bool on);
+bool oz_tc_timed_out(cudaStream_t st);
 
 // Call sites of the stabilisation GEMMs. The fast FP64-accurate variants
 // (double-float, digit slices) are accurate relative to the largest entries
@@ -51,6 +59,7 @@ enum GemmSite {
   GS_APPLY_QT,       // Q^T B in the solve
   GS_TRSM,           // block triangular solve
   GS_FINAL,          // G = U_l Z
+  GS_CHOLQR,         // CholeskyQR2: Gram matrices, Cholesky recursion, Q and R products
   GS_COUNT
 };
 void set_gemm_site(int site);
@@ -59,6 +68,17 @@ void set_gemm_site_mask(unsigned mask);
 // digit-slice GEMM is on (needs a double-float workspace)
 void set_gemm_df_site_mask(unsigned mask);
 cudaError_t scale_matrix(double *C, int M, int N, int ldc, double beta, cudaStream_t st);
+
+// Split-K workspace of the calling host thread (doubles); splitk_ws_doubles()
+// covers every split the GEMMs here choose by themselves.
+void set_splitk_workspace(double *ws, size_t n);
+size_t splitk_ws_doubles();
+// The partial-product buffer for `splits` splits of an M x N output, or NULL
+// when splits <= 1 or the bound workspace is too small.
+double *splitk_partials(int splits, int M, int N);
+// C = beta C + sum_{z < splits} part[z] (fixed order), part dense M x N per split.
+cudaError_t splitk_reduce(const double *part, int splits, int M, int N, double beta, double *C,
+                          int ldc, cudaStream_t st);
 
 // Householder QR workspace for an n x n matrix: V (unit lower trapezoidal,
 // explicit; panel p in columns p..p+nb), tau, the compact-WY factor T of each
@@ -83,6 +103,21 @@ cudaError_t qr_apply_qt(double *B, int n, int ncols, int ldb, QRWork &w, cudaStr
 // Z = R^{-1} B (R upper triangular in A's upper triangle), B destroyed; Z n x ncols.
 cudaError_t qr_solve_r(const double *A, int n, double *B, double *Z, int ncols, QRWork &w,
                        cudaStream_t st);
+
+// Cholesky A = R^T R of the symmetric positive definite n x n matrix A (upper
+// triangle read, ld lda): R to A's upper triangle (zeros below), R^{-1} to Ri
+// (upper, zeros below, ld ldr). Wk: n x n scratch (ld ldw). A non-positive
+// pivot sets *status = 1 (device int).
+cudaError_t chol_inv(double *A, int lda, double *Ri, int ldr, double *Wk, int ldw, int n, int *status,
+                     cudaStream_t st);
+// W += c tr(W) I (the shift of a shifted Cholesky QR pass; tr(W) >= ||X||_2^2
+// for W = X^T X).
+cudaError_t shift_diag(double *W, int n, int ld, double c, cudaStream_t st);
+// CholeskyQR2 of the n x n X (row-major, ld n): Q (n x n) and R (n x n upper,
+// zeros below) with X = Q R. Scratch Q1, W, Ri, Wk: n x n each; none may alias
+// X, Q or R. X is only read.
+cudaError_t cholqr2(const double *X, int n, double *Q, double *R, double *Q1, double *W, double *Ri,
+                    double *Wk, int *status, cudaStream_t st);
 
 // ---- elementwise / small helpers
 cudaError_t set_identity(double *A, int n, int ld, cudaStream_t st);

@@ -100,11 +100,10 @@ dqmc_status dqmc_op_propagate_f32(int L, double scale, int side, const float *X,
   return DQMC_OK;
 } DQ_API_CATCH
 
-dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, int ld_g,
-                                     int8_t *s, double lambda, uint64_t seed, uint32_t chain,
-                                     uint32_t sweep_pass, int slice1, const uint8_t *forced,
-                                     double *alpha, double *beta, int *accept_count, int *status,
-                                     void *stream) try {
+static dqmc_status op_metropolis(int N, int site0, int kb, const double *g, int ld_g, int8_t *s,
+                                 double lambda, uint64_t seed, uint32_t chain, uint32_t sweep_pass,
+                                 int slice1, const uint8_t *forced, double *alpha, double *beta,
+                                 int *accept_count, int *status, void *stream, bool df) {
   if (N < 1 || kb < 1 || kb > 64 || site0 < 0 || site0 + kb > N)
     return fail(DQMC_EINVAL, "need 1 <= kb <= 64 and 0 <= site0, site0 + kb <= N");
   if (!g || !s || !alpha || !beta || !accept_count || !status) return fail(DQMC_EINVAL, "null pointer");
@@ -125,8 +124,26 @@ dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, 
   a.c3 = (chain & 0xffffffu) | (kDomainMetropolis << 24);
   a.slice0 = slice1 - 1;
   DQ_CUDA(launch_metropolis(a, g, false, s, forced, alpha, beta, accept_count, status, nullptr,
-                            static_cast<cudaStream_t>(stream)));
+                            static_cast<cudaStream_t>(stream), df));
   return DQMC_OK;
+}
+
+dqmc_status dqmc_op_metropolis_block(int N, int site0, int kb, const double *g, int ld_g,
+                                     int8_t *s, double lambda, uint64_t seed, uint32_t chain,
+                                     uint32_t sweep_pass, int slice1, const uint8_t *forced,
+                                     double *alpha, double *beta, int *accept_count, int *status,
+                                     void *stream) try {
+  return op_metropolis(N, site0, kb, g, ld_g, s, lambda, seed, chain, sweep_pass, slice1, forced, alpha,
+                       beta, accept_count, status, stream, false);
+} DQ_API_CATCH
+
+dqmc_status dqmc_op_metropolis_block_df(int N, int site0, int kb, const double *g, int ld_g,
+                                        int8_t *s, double lambda, uint64_t seed, uint32_t chain,
+                                        uint32_t sweep_pass, int slice1, const uint8_t *forced,
+                                        double *alpha, double *beta, int *accept_count, int *status,
+                                        void *stream) try {
+  return op_metropolis(N, site0, kb, g, ld_g, s, lambda, seed, chain, sweep_pass, slice1, forced, alpha,
+                       beta, accept_count, status, stream, true);
 } DQ_API_CATCH
 
 }  // extern "C"
@@ -176,7 +193,9 @@ dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *G
 dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, double alpha,
                              const double *A, int lda, const double *B, int ldb, double beta,
                              double *C, int ldc, void *stream) try {
-  if (mode < 0 || mode > 2) return fail(DQMC_EINVAL, "mode must be 0 (FP64), 1 (double-float) or 2 (digit slices)");
+  if (mode < 0 || mode > 3)
+    return fail(DQMC_EINVAL, "mode must be 0 (FP64), 1 (double-float), 2 (digit slices, mma.sync) or 3 "
+                             "(digit slices, tcgen05)");
   if (M < 0 || N < 0 || K < 0) return fail(DQMC_EINVAL, "negative size");
   if ((M && N && K) && (!A || !B)) return fail(DQMC_EINVAL, "null operand");
   if (M && N && !C) return fail(DQMC_EINVAL, "null C");
@@ -184,22 +203,29 @@ dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, doub
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void *ws = nullptr;
   int *ex = nullptr;
+  double *sk = nullptr;
   cudaError_t e = cudaSuccess;
+  DQ_CUDA(cudaMallocAsync((void **)&sk, splitk_ws_doubles() * sizeof(double), st));
+  set_splitk_workspace(sk, splitk_ws_doubles());
   if (mode == 1) {
     DQ_CUDA(cudaMallocAsync(&ws, ((size_t)M * K + (size_t)K * N + 1) * sizeof(float2), st));
     set_df_workspace(static_cast<float2 *>(ws), (size_t)M * K + (size_t)K * N + 1);
     e = dfgemm(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, nullptr, st, 0, 304);
     set_df_workspace(nullptr, 0);
-  } else if (mode == 2) {
+  } else if (mode == 2 || mode == 3) {
     const size_t bytes = oz_workspace_bytes(M, N, K) + 16;
     DQ_CUDA(cudaMallocAsync(&ws, bytes, st));
     DQ_CUDA(cudaMallocAsync((void **)&ex, ((size_t)M + N + 1) * sizeof(int), st));
     set_oz_workspace(ws, bytes, ex, (size_t)M + N + 1);
+    set_gemm_oz_tc(mode == 3);
     e = ozgemm(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, nullptr, st);
+    set_gemm_oz_tc(false);
     set_oz_workspace(nullptr, 0, nullptr, 0);
   } else {
     e = dgemm(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, nullptr, st);
   }
+  set_splitk_workspace(nullptr, 0);
+  cudaFreeAsync(sk, st);
   if (ws) cudaFreeAsync(ws, st);
   if (ex) cudaFreeAsync(ex, st);
   if (e != cudaSuccess) return cuda_fail(e, "gemm");

@@ -173,7 +173,7 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
 // (9 levels x 16 FP32 live), 0.15 ldmatrix per MMA. After every 64 positions
 // of K the exact level sums are folded: levels 2..7 into an int64
 // accumulator (weight 2^{7(7-l)}), 8..10 into FP32; the epilogue forms
-// (I + F) 2^{-49} 2^{E_i + F_j} once per output (split K: FP64 atomics).
+// (I + F) 2^{-49} 2^{E_i + F_j} once per output (split K: partial products, summed in order).
 constexpr int OZ_SC = 32;           // staging sub-chunk of K
 constexpr int OZ_LDS = OZ_SC + 8;   // padded smem row (bf16): 80 B, conflict-free ldmatrix
 constexpr int OZ_BUF = OZ_S * (OZ_BM + OZ_BN) * OZ_LDS;  // one buffer, bf16 elements
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256)
                       const unsigned short *__restrict__ Bd, const int *__restrict__ ea,
                       const int *__restrict__ eb, double alpha, double beta, double *__restrict__ C,
                       int ldc, const double *__restrict__ rs, const double *__restrict__ cs,
-                      int kchunks, int atomic) {
+                      int kchunks, double *__restrict__ part) {
   extern __shared__ __align__(16) unsigned short osm[];  // two buffers of OZ_BUF
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 1, wn = warp & 1;               // 4 x 2 warps
@@ -323,11 +323,300 @@ __global__ void __launch_bounds__(256)
       if (rs) v *= rs[i];
       if (cs) v *= cs[j];
       double *cp = C + (size_t)i * ldc + j;
-      if (atomic)
-        atomicAdd(cp, v);
+      if (part)
+        part[((size_t)blockIdx.z * M + i) * N + j] = v;
       else
         *cp = (beta != 0.0) ? v + beta * (*cp) : v;
     }
+}
+
+// ====================================================================== tcgen05 path
+// The same digit-slice product on the 5th-generation tensor cores: bf16
+// tcgen05.mma (kind::f16, FP32 accumulate) with the accumulators in tensor
+// memory. CTA tile 128 x 48 (M x N), 128 threads. Thread 0 issues the MMAs;
+// all threads stage the operands with cp.async and fold the accumulators.
+//
+// Shared memory: two stages of 32 positions of K, each holding the 9 digit
+// planes of the A tile (128 x 32 bf16) and of the B tile (48 x 32 bf16) in the
+// canonical K-major layout without swizzle: 8 x 16-byte core matrices, 128 B
+// each, the four along K adjacent (leading byte offset 128), 8-row groups
+// 512 B apart (stride byte offset). One K = 16 MMA reads two core-matrix
+// columns: the descriptor start advances by 256 B for the second half.
+//
+// Tensor memory: 512 columns; level l = p + q (2..10) accumulates in columns
+// 48 (l - 2) .. 48 (l - 2) + 47, lane = output row. Every 64 positions of K
+// (two stages) the sums of levels 2..6 are exact integers below 2^24; all
+// threads wait for the MMAs (mbarrier of tcgen05.commit), load their row of
+// those levels (tcgen05.ld 32x32b, lanes 32 w .. 32 w + 31 for warp w) and
+// fold them into an exact int64 accumulator (weights 2^{7(6-l)}); the next
+// period's first MMA of each of these levels overwrites (enable-input-d
+// false). Levels 7..10 keep accumulating in FP32 over the whole K: their
+// rounding stays below 2^-53 of the level-2 sum, and they are read once.
+//
+// Every wait on an mbarrier is bounded; a wait that gives up sets a device
+// flag (read by oz_tc_timed_out) and the CTA stops issuing work, drains its
+// copies, frees its tensor memory and returns.
+constexpr int TC_BM = 128, TC_BN = 48, TC_BK = 32;
+constexpr int TC_A_PLANE = TC_BM * TC_BK * 2;                 // bytes
+constexpr int TC_B_PLANE = TC_BN * TC_BK * 2;
+constexpr int TC_STAGE = OZ_S * (TC_A_PLANE + TC_B_PLANE);    // 101376 B
+constexpr int TC_SMEM = 2 * TC_STAGE + 128;                   // + mbarriers and the TMEM address
+constexpr int TC_TMEM_COLS = 512;
+constexpr uint32_t TC_IDESC = (1u << 4)                       // D: FP32
+                              | (1u << 7) | (1u << 10)        // A, B: bf16
+                              | ((uint32_t)(TC_BN >> 3) << 17)  // N >> 3
+                              | ((uint32_t)(TC_BM >> 4) << 24); // M >> 4; both operands K-major
+constexpr int TC_WAIT_LIMIT = 1 << 22;
+
+__device__ int g_oz_tc_timeout = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor: start, LBO 128 B, SBO 512 B, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(512 >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes));
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Stage `st` (positions k0 .. k0 + 31) into buffer b: every thread copies
+// 16-byte pieces (8 positions of one row of one plane); rows beyond M / N
+// are zero-filled.
+__device__ __forceinline__ void tc_stage(uint32_t sbase, int b, const unsigned short *Ad,
+                                         const unsigned short *Bd, int M, int N, int Kp, int m0,
+                                         int n0, int k0, size_t aplane, size_t bplane) {
+  constexpr int ROWS = TC_BM + TC_BN, PER_PLANE = ROWS * (TC_BK / 8);
+  const uint32_t stage = sbase + b * TC_STAGE;
+  for (int e = threadIdx.x; e < OZ_S * PER_PLANE; e += blockDim.x) {
+    const int p = e / PER_PLANE, rem = e % PER_PLANE;
+    const int r = rem >> 2, kg = rem & 3;
+    uint32_t dst;
+    const unsigned short *src;
+    int ok;
+    if (r < TC_BM) {
+      dst = stage + p * TC_A_PLANE + (((r >> 3) * 4 + kg) << 7) + ((r & 7) << 4);
+      ok = (m0 + r) < M;
+      src = Ad + p * aplane + (size_t)(ok ? m0 + r : 0) * Kp + k0 + kg * 8;
+    } else {
+      const int rb = r - TC_BM;
+      dst = stage + OZ_S * TC_A_PLANE + p * TC_B_PLANE + (((rb >> 3) * 4 + kg) << 7) + ((rb & 7) << 4);
+      ok = (n0 + rb) < N;
+      src = Bd + p * bplane + (size_t)(ok ? n0 + rb : 0) * Kp + k0 + kg * 8;
+    }
+    cp_async16_zfill(dst, src, ok ? 16 : 0);
+  }
+  cp_async_commit();
+}
+
+__global__ void __launch_bounds__(128, 1)
+    oz_gemm_tc_kernel(int M, int N, int Kp, const unsigned short *__restrict__ Ad,
+                      const unsigned short *__restrict__ Bd, const int *__restrict__ ea,
+                      const int *__restrict__ eb, double alpha, double beta, double *__restrict__ C,
+                      int ldc, const double *__restrict__ rs, const double *__restrict__ cs,
+                      int kchunks, double *__restrict__ part) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+  const size_t aplane = (size_t)M * Kp, bplane = (size_t)N * Kp;
+  const uint32_t sbase = smem_u32(tsm);
+  unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tsm + 2 * TC_STAGE);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(tsm + 2 * TC_STAGE + 64);
+  const uint32_t mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb1));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tbase = *tslot;
+
+  long long I[TC_BN];
+#pragma unroll
+  for (int c = 0; c < TC_BN; ++c) I[c] = 0;
+
+  const int kbeg = blockIdx.z * kchunks * OZ_KC;
+  const int kend = min(Kp, kbeg + kchunks * OZ_KC);
+  const int nst = (kend - kbeg) / TC_BK;  // even: Kp and the chunk bounds are multiples of 64
+  bool bad = false;
+  if (nst > 0) tc_stage(sbase, 0, Ad, Bd, M, N, Kp, m0, n0, kbeg, aplane, bplane);
+  for (int st = 0; st < nst && !bad; ++st) {
+    const int b = st & 1;
+    if (st + 1 < nst) {
+      // buffer b ^ 1 last fed the MMAs of stage st - 1: wait for them first
+      bool ok = true;
+      if (st >= 1) ok = mbar_wait(b ? mb0 : mb1, ((st - 1) >> 1) & 1);
+      if (__syncthreads_or(!ok)) {
+        bad = true;
+        break;
+      }
+      tc_stage(sbase, b ^ 1, Ad, Bd, M, N, Kp, m0, n0, kbeg + (st + 1) * TC_BK, aplane, bplane);
+      cp_async_wait_one();
+    } else {
+      cp_async_wait_all();
+    }
+    // the copies become visible to the tensor core (async proxy), then to thread 0
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t abase = sbase + b * TC_STAGE, bbase = abase + OZ_S * TC_A_PLANE;
+      const bool first = (st & 1) == 0;
+#pragma unroll 1
+      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+#pragma unroll 1
+        for (int p = 0; p < OZ_S; ++p) {
+          const uint64_t ad = tc_desc(abase + p * TC_A_PLANE + kk * 256);
+#pragma unroll 1
+          for (int q = 0; p + q <= OZ_S - 1; ++q) {
+            const uint64_t bd = tc_desc(bbase + q * TC_B_PLANE + kk * 256);
+            // levels 2..6 restart every 64 positions, 7..10 only at the first
+            const uint32_t acc = (first && kk == 0 && p == 0 && (q <= 4 || st == 0)) ? 0u : 1u;
+            tc_mma(tbase + (uint32_t)((p + q) * TC_BN), ad, bd, acc);
+          }
+        }
+      }
+      tc_commit(b ? mb1 : mb0);
+    }
+    if (st & 1) {
+      // end of 64 positions: fold the exact level sums
+      const bool ok = mbar_wait(b ? mb1 : mb0, (st >> 1) & 1);
+      if (__syncthreads_or(!ok)) {
+        bad = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+      for (int idx = 0; idx < 5; ++idx) {
+        const int l = idx + 2;
+#pragma unroll
+        for (int ch = 0; ch < TC_BN / 16; ++ch) {
+          float v[16];
+          tc_ld16(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) I[ch * 16 + i] += ((long long)__float2int_rn(v[i])) << (7 * (6 - l));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+    }
+  }
+  if (bad) {
+    if (tid == 0) atomicExch(&g_oz_tc_timeout, 1);
+    cp_async_wait_all();
+  }
+  // levels 7..10 (weights 2^{-7(l-6)}) are read once, 16 columns at a time
+  // (the last period's fold waited for every MMA), and the outputs of those
+  // columns are formed: (I + F) 2^{-42} 2^{E_i + F_j}
+  const int i = m0 + warp * 32 + lane;
+  const bool row_ok = !bad && nst > 0 && i < M;
+  const double r = (rs && i < M) ? rs[i] * alpha : alpha;
+  if (!bad && nst > 0) {
+    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int ch = 0; ch < TC_BN / 16; ++ch) {
+      float F[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) F[c] = 0.f;
+#pragma unroll
+      for (int idx = 5; idx < OZ_S; ++idx) {
+        const float w = __int_as_float((127 - 7 * (idx - 4)) << 23);
+        float v[16];
+        tc_ld16(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) F[c] = fmaf(v[c], w, F[c]);
+      }
+      if (row_ok) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int j = n0 + ch * 16 + c;
+          if (j >= N) continue;
+          const double dot = (double)I[ch * 16 + c] + (double)F[c];
+          const int e2 = (ea[i] - 1022) + (eb[j] - 1022) - 42;
+          double v = ldexp(dot, e2) * r;
+          if (cs) v *= cs[j];
+          double *cp = C + (size_t)i * ldc + j;
+          if (part)
+            part[((size_t)blockIdx.z * M + i) * N + j] = v;
+          else
+            *cp = (beta != 0.0) ? v + beta * (*cp) : v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TC_TMEM_COLS));
+  }
+  if (!bad && nst == 0 && i < M) {
+    // an empty K range: the product is zero
+    for (int c = 0; c < TC_BN; ++c) {
+      const int j = n0 + c;
+      if (j >= N) break;
+      double *cp = C + (size_t)i * ldc + j;
+      if (part)
+        part[((size_t)blockIdx.z * M + i) * N + j] = 0.0;
+      else
+        *cp = (beta != 0.0) ? beta * (*cp) : 0.0;
+    }
+  }
+}
+
+static thread_local bool t_oz_tc = false;
+void set_gemm_oz_tc(bool on) { t_oz_tc = on; }
+
+bool oz_tc_timed_out(cudaStream_t st) {
+  int v = 0;
+  if (cudaMemcpyFromSymbolAsync(&v, g_oz_tc_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return false;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return false;
+  return v != 0;
 }
 
 static thread_local unsigned short *t_ozws = nullptr;
@@ -376,11 +665,13 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
     DQ_KSCOPE(KF_SLICE, st);
     oz_slice_kernel<<<stiles, 256, 0, st>>>(oa, ob);
   }
-  const int smem = 2 * OZ_BUF * (int)sizeof(unsigned short);  // two staging buffers
-  e = ensure_smem_attr((const void *)oz_gemm_rb_kernel, smem);
+  const bool tc = t_oz_tc;
+  const int BM = tc ? TC_BM : OZ_BM, BN = tc ? TC_BN : OZ_BN;
+  const int smem = tc ? TC_SMEM : 2 * OZ_BUF * (int)sizeof(unsigned short);  // two staging buffers
+  e = ensure_smem_attr(tc ? (const void *)oz_gemm_tc_kernel : (const void *)oz_gemm_rb_kernel, smem);
   if (e != cudaSuccess) return e;
   // one CTA per SM (shared memory); split K when the tiles do not fill the GPU
-  const int tiles = ((N + OZ_BN - 1) / OZ_BN) * ((M + OZ_BM - 1) / OZ_BM);
+  const int tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
   const int nchunks = Kp / OZ_KC;
   int splits = 1;
   if (tiles < 152) {
@@ -389,20 +680,26 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
     if (splits > maxs) splits = maxs;
     if (splits < 1) splits = 1;
   }
-  const int kchunks = (nchunks + splits - 1) / splits;
+  int kchunks = (nchunks + splits - 1) / splits;
   splits = (nchunks + kchunks - 1) / kchunks;
-  const int atomic = splits > 1;
-  if (atomic) {
-    e = scale_matrix(C, M, N, ldc, beta, st);
-    if (e != cudaSuccess) return e;
+  double *part = splitk_partials(splits, M, N);
+  if (splits > 1 && !part) {
+    splits = 1;
+    kchunks = nchunks;
   }
-  dim3 grid((N + OZ_BN - 1) / OZ_BN, (M + OZ_BM - 1) / OZ_BM, splits);
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
   DQ_KSCOPE(KF_GEMM, st);
   add_work(KF_GEMM, 2.0 * M * (double)N * K,
            8.0 * ((double)M * K + (double)K * N + (beta != 0.0 ? 2.0 : 1.0) * (double)M * N));
-  oz_gemm_rb_kernel<<<grid, 256, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
-                                          kchunks, atomic);
-  return cudaGetLastError();
+  if (tc)
+    oz_gemm_tc_kernel<<<grid, 128, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
+                                              kchunks, part);
+  else
+    oz_gemm_rb_kernel<<<grid, 256, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
+                                              kchunks, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !part) return e;
+  return splitk_reduce(part, splits, M, N, beta, C, ldc, st);
 }
 
 }  // namespace dq

@@ -3,24 +3,19 @@
 // Sites are proposed in index order in blocks S of k consecutive sites. For a
 // block, everything the sequential Sherman-Morrison updates need lies in the
 // k x k sub-block g = G[S,S] (submatrix form of the delayed update): the
-// current diagonal G~_jj and, per accepted flip m at block site t_m, the
-// restricted update column As_m = (delta/r) G~[S, t_m] and row
-// Bs_m = e_t - G~[t_m, S]. Two coefficient recursions alpha_m, beta_m in R^k,
-//     alpha_m = c_m (e_t - sum_{m'<m} alpha_m' Bs_m'[t]),
-//     beta_m  = e_t + sum_{m'<m} As_m'[t] beta_m',
-// give the full-space updates a_m = G[:,S] alpha_m and
-// b_m^T = beta_m^T (E_S - G[S,:]), so that after the block
-//     G' = G - A B^T,  A = G[:,S] [alpha_0 .. alpha_{m-1}],  B^T = [beta_m] (E_S - G[S,:]),
-// which equals the sequential rank-one updates exactly (Woodbury form with
-// Gamma = sum alpha beta^T never formed). The flush is a rank-m update with
-// m the number of accepted flips.
+// decisions follow the current block g~ under the accepted flips, and the m
+// accepted flips P then compose into one Woodbury update of the whole G,
+//     G' = G - G[:,P] Gamma (E_P - G[P,:]),  Gamma = (Delta^{-1} + I - G[P,P])^{-1},
+// which equals the sequential rank-one updates exactly. The flush is that
+// rank-m update, written as G' = G - A B^T with A = G[:,S] alpha^T and
+// B^T = beta (E_S - G[S,:]), where alpha^T beta = Gamma on (P, P).
 //
-// Kernels: the Metropolis block (one CTA, FP64 or double-float recursions),
-// the A factor (and, for the double-float flush, the B factor), the
-// look-ahead G'[S',S'] of the next block from the pre-flush G (so that the
-// next block's decisions can run while this block's flush streams G), and the
-// flush itself -- FP64 / FP32 by column stripes, or double-float by 64 x 64
-// tiles -- whose epilogue gathers G[:,S'] and G[S',:] of the next block.
+// Kernels: the Metropolis block (one CTA, FP64), the A factor (and, for the
+// double-float flush, the B factor), the look-ahead G'[S',S'] of the next
+// block from the pre-flush G (so that the next block's decisions can run
+// while this block's flush streams G), and the flush itself -- FP64 / FP32 by
+// column stripes, or double-float by 64 x 64 tiles -- whose epilogue gathers
+// G[:,S'] and G[S',:] of the next block.
 #include <algorithm>
 #include <type_traits>
 
@@ -66,15 +61,37 @@ template cudaError_t launch_gather<float>(int, int, int, int, const float *, flo
                                           cudaStream_t);
 
 // ----------------------------------------------------------------- Metropolis block
-// Arithmetic of the block's recursions: FP64, or double-float (df64, ~2^-47,
-// on the FP32 units) in mixed precision. The decision u < R compares the
-// FP64 value of R in both.
+// Decisions and the Woodbury coefficients of one block S of kb <= 64 sites.
+//
+// The decisions need only the current k x k block g~ = G~[S,S]: the ratio of
+// site j is r = 1 + delta_j (1 - g~_jj) with delta_j = e^{-2 lambda s_j} - 1,
+// R = e^{2 lambda s_j} r^2, and an accepted flip changes the block by the
+// Sherman-Morrison step g~ <- g~ - (delta/r) g~[:,j] (e_j - g~[j,:]). Only the
+// trailing part (rows and columns after j) matters for later decisions, so
+// each accepted flip updates that part in shared memory (right-looking).
+//
+// The m accepted flips P = (p_1 .. p_m), in order, then compose into one
+// Woodbury update of the whole G:
+//     G' = G - G[:,P] Gamma (E_P - G[P,:]),   Gamma = (Delta^{-1} + I - G[P,P])^{-1},
+// Delta = diag(delta_p), G the block's input. Gauss-Jordan elimination of
+// Delta^{-1} + I - G[P,P] in acceptance order without pivoting has exactly the
+// sequential quantities r_p / delta_p as pivots (the Schur complements), so
+// it is as stable as the one-at-a-time updates. Gamma is computed in FP64.
+// Output in the form of the flush kernels: row r of alpha is column r of
+// Gamma scattered to the block positions of P, row r of beta selects p_r:
+//     alpha^T beta = Gamma on (P, P), zero elsewhere.
+//
+// Arithmetic of the block: FP64, or double-float (df64, ~2^-47, on the FP32
+// units) in mixed precision, where the FP64 pipe (1/64 of FP32 on this part)
+// would make the serial decision chain the critical path.
 template <typename T> struct MetroMath;
 template <> struct MetroMath<double> {
   static __device__ __forceinline__ double from(double x) { return x; }
   static __device__ __forceinline__ double to(double x) { return x; }
   static __device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ bool positive(double a) { return a > 0.0; }
+  static __device__ __forceinline__ bool finite(double a) { return isfinite(a); }
 };
 template <> struct MetroMath<df64> {
   static __device__ __forceinline__ df64 from(double x) { return df_from(x); }
@@ -87,143 +104,165 @@ template <> struct MetroMath<df64> {
     const float q2 = r.hi / b.hi;
     return fast_two_sum(q1, q2);
   }
+  static __device__ __forceinline__ bool positive(df64 a) { return a.hi > 0.f || (a.hi == 0.f && a.lo > 0.f); }
+  static __device__ __forceinline__ bool finite(df64 a) { return isfinite(a.hi); }
 };
 
-// One CTA of 4 warps. Lane u of every warp owns block sites u and u + 32.
-// On an accepted flip the four recursions of the accepted site run in
-// parallel, one per warp (warp 0: As, warp 1: Bs, warp 2: alpha, warp 3:
-// beta), each a length-m dot product per site; warp 0 keeps the current
-// diagonal G~_uu in registers and takes the decisions.
-// Shared: g (kb x (kb+1)), As/Bs/al/be (K x kb each, row m = accepted flip m).
-template <typename T>
-__global__ void __launch_bounds__(128)
+// One CTA of 4 x NC threads (NC = 32 or 64 block columns): thread (w, v) owns
+// column v and the rows i = w (mod 4) of the block, so that the work of a
+// trailing update is spread over the four SM sub-partitions. The decision of
+// site j is taken by the thread that also wrote g~_jj last (column j, row
+// group j mod 4), and the one barrier per site publishes it.
+template <int NC, typename T>
+__global__ void __launch_bounds__(4 * NC)
     metropolis_block_kernel(MetroArgs a, const void *__restrict__ g_, int g_is_f32, int8_t *s,
                             const uint8_t *__restrict__ forced, double *__restrict__ alpha_out,
                             double *__restrict__ beta_out, int *accept_count, int *status,
                             unsigned long long *total) {
   using MM = MetroMath<T>;
+  constexpr int LD = NC + 1;
   extern __shared__ __align__(16) unsigned char msm_raw[];
-  T *sm = reinterpret_cast<T *>(msm_raw);
-  const int kb = a.kb;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ldg = kb + 1;
-  T *gs = sm;              // kb * ldg
-  T *As = gs + kb * ldg;   // [m][u]
-  T *Bs = As + kb * kb;
-  T *al = Bs + kb * kb;
-  T *be = al + kb * kb;
-  // decision and coefficient of site j, double-buffered by the parity of j:
-  // a rejected site has no second barrier, so the slot written at j + 2 must
-  // differ from the one still being read at j
+  T *g = reinterpret_cast<T *>(msm_raw);  // NC x LD: current block, then Delta^{-1} + I - G[P,P] -> Gamma
+  T *g0 = g + NC * LD;                    // NC x LD: the input block
+  __shared__ T s_c[2], s_pinv;
   __shared__ int s_dec[2];
-  __shared__ T s_coef[2];
+  __shared__ int s_P[NC];
+  __shared__ T s_delta[NC];
+  __shared__ double s_u[NC];
+  __shared__ int s_spin[NC];
+  const int kb = a.kb;
+  const int tid = threadIdx.x, v = tid % NC, w = tid / NC;
 
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+  for (int e = tid; e < kb * kb; e += 4 * NC) {
     const int r = e / kb, c = e % kb;
     const size_t off = (size_t)r * a.ld_g + c;
-    gs[r * ldg + c] = MM::from(g_is_f32 ? (double)static_cast<const float *>(g_)[off]
-                                        : static_cast<const double *>(g_)[off]);
+    const double x = g_is_f32 ? (double)static_cast<const float *>(g_)[off]
+                              : static_cast<const double *>(g_)[off];
+    g[r * LD + c] = MM::from(x);
+    g0[r * LD + c] = MM::from(x);
   }
-  // warp 0: per-site state (sites lane and lane + 32)
-  T dtil[2] = {T(0), T(0)};
-  double urand[2] = {0.0, 0.0};
-  int si[2] = {1, 1};
-  if (warp == 0) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int u = lane + 32 * h;
-      if (u < kb) {
-        const uint4 r = philox4x32_10(
-            make_uint4((uint32_t)(a.s0 + u), (uint32_t)a.slice0, a.c2, a.c3), a.k0, a.k1);
-        urand[h] = uniform53(r.x, r.y);
-        si[h] = (int)s[a.s0 + u];
-      }
-    }
+  if (w == 0 && v < kb) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(a.s0 + v), (uint32_t)a.slice0, a.c2, a.c3),
+                                  a.k0, a.k1);
+    s_u[v] = uniform53(r.x, r.y);
+    s_spin[v] = (int)s[a.s0 + v];
   }
   __syncthreads();
-  if (warp == 0) {
-    if (lane < kb) dtil[0] = gs[lane * ldg + lane];
-    if (lane + 32 < kb) dtil[1] = gs[(lane + 32) * ldg + lane + 32];
-  }
 
-  const T e2l = MM::from(a.e2l), em2l = MM::from(a.em2l);
+  const T one = MM::from(1.0);
   const T dpos = MM::from(a.em2l - 1.0), dneg = MM::from(a.e2l - 1.0);  // delta for s = +1 / -1
-  const T one = T(1), zero = T(0);
+  const T epos = MM::from(a.e2l), eneg = MM::from(a.em2l);
   int m = 0;
+  bool failed = false;
   for (int j = 0; j < kb; ++j) {
-    if (warp == 0 && lane == (j & 31)) {
-      const int h = j >> 5;
-      // delta = e^{-2 lambda s} - 1, r = 1 + delta (1 - G~_jj), R = e^{2 lambda s} r^2
-      const T delta = si[h] > 0 ? dpos : dneg;
-      const T r = one + delta * (one - dtil[h]);
-      const double R = MM::to((si[h] > 0 ? e2l : em2l) * r * r);
+    if (v == j && w == (j & 3)) {
+      // delta = e^{-2 lambda s} - 1, r = 1 + delta (1 - g~_jj), R = e^{2 lambda s} r^2
+      const int sj = s_spin[j];
+      const T delta = sj > 0 ? dpos : dneg;
+      const T r = MM::mad(delta, one - g[j * LD + j], one);
+      const T R = (sj > 0 ? epos : eneg) * r * r;
       int dec;
-      if (!(R > 0.0) || !isfinite(R)) {
+      if (!MM::positive(R) || !MM::finite(R))
         dec = -1;
-      } else if (forced) {
+      else if (forced)
         dec = forced[j] ? 1 : 0;
-      } else {
-        dec = (urand[h] < R) ? 1 : 0;
-      }
+      else
+        dec = MM::positive(R - MM::from(s_u[j])) ? 1 : 0;  // accept iff u < R
       s_dec[j & 1] = dec;
-      if (dec > 0) s_coef[j & 1] = MM::div(delta, r);
+      if (dec > 0) s_c[j & 1] = MM::div(delta, r);
     }
     __syncthreads();
     const int dec = s_dec[j & 1];
     if (dec < 0) {
-      if (threadIdx.x == 0) *status = 1;
+      failed = true;
       break;
     }
     if (!dec) continue;
-    const T c = s_coef[j & 1];
+    if (tid == 0) {
+      s_P[m] = j;
+      s_delta[m] = s_spin[j] > 0 ? dpos : dneg;
+      s_spin[j] = -s_spin[j];
+      s[a.s0 + j] = (int8_t)s_spin[j];
+    }
+    ++m;
+    // trailing update g~[i][v] += c g~[j][v] g~[i][j] for i, v > j
+    // (the e_j term of the step only touches column j, which is done with)
+    if (v > j && v < kb) {
+      const T cg = s_c[j & 1] * g[j * LD + v];
+      int i = j + 1;
+      i += (w - i) & 3;  // first row > j in this thread's row group
+      for (; i < kb; i += 4) g[i * LD + v] = MM::mad(cg, g[i * LD + j], g[i * LD + v]);
+    }
+  }
+  __syncthreads();
+
+  // Gamma = (Delta^{-1} + I - G[P,P])^{-1} by in-place Gauss-Jordan, P in order
+  for (int e = tid; e < m * m; e += 4 * NC) {
+    const int r = e / m, c = e % m;
+    const T dinv = MM::div(one, s_delta[r]);
+    g[r * LD + c] = (r == c ? one + dinv : MM::from(0.0)) - g0[s_P[r] * LD + s_P[c]];
+  }
+  __syncthreads();
+  for (int p = 0; p < m; ++p) {
+    if (tid == 0) s_pinv = MM::div(one, g[p * LD + p]);
+    __syncthreads();
+    const T pinv = s_pinv;
+    if (w == (p & 3) && v < m) g[p * LD + v] = (v == p) ? pinv : g[p * LD + v] * pinv;
+    T f[NC / 4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int u = lane + 32 * h;
-      if (u >= kb) continue;
-      const T dj = (u == j) ? one : zero;
-      if (warp == 0) {         // As_m[u] = c (g[u][j] - sum As_m'[u] Bs_m'[j])
-        T v = gs[u * ldg + j];
-        for (int mm = 0; mm < m; ++mm) v = MM::mad(-As[mm * kb + u], Bs[mm * kb + j], v);
-        As[m * kb + u] = c * v;
-      } else if (warp == 1) {  // Bs_m[u] = delta_uj - (g[j][u] - sum As_m'[j] Bs_m'[u])
-        T v = gs[j * ldg + u];
-        for (int mm = 0; mm < m; ++mm) v = MM::mad(-As[mm * kb + j], Bs[mm * kb + u], v);
-        Bs[m * kb + u] = dj - v;
-      } else if (warp == 2) {  // al_m[u] = c (delta_uj - sum al_m'[u] Bs_m'[j])
-        T v = dj;
-        for (int mm = 0; mm < m; ++mm) v = MM::mad(-al[mm * kb + u], Bs[mm * kb + j], v);
-        al[m * kb + u] = c * v;
-      } else {                 // be_m[u] = delta_uj + sum As_m'[j] be_m'[u]
-        T v = dj;
-        for (int mm = 0; mm < m; ++mm) v = MM::mad(As[mm * kb + j], be[mm * kb + u], v);
-        be[m * kb + u] = v;
+    for (int q = 0; q < NC / 4; ++q) {
+      const int i = w + 4 * q;
+      f[q] = (i < m && i != p) ? g[i * LD + p] : MM::from(0.0);
+    }
+    __syncthreads();
+    if (v < m) {
+      const T rp = g[p * LD + v];
+#pragma unroll
+      for (int q = 0; q < NC / 4; ++q) {
+        const int i = w + 4 * q;
+        if (i < m && i != p)
+          g[i * LD + v] = (v == p) ? -(f[q] * pinv) : MM::mad(-f[q], rp, g[i * LD + v]);
       }
     }
     __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int u = lane + 32 * h;
-        if (u < kb) dtil[h] = MM::mad(-As[m * kb + u], Bs[m * kb + u], dtil[h]);
-        if (u == j) {
-          si[h] = -si[h];
-          s[a.s0 + u] = (int8_t)si[h];
-        }
-      }
-    }
-    ++m;
   }
-  // outputs: rows m' < m of alpha and beta (row stride K); the rest zero
-  for (int e = threadIdx.x; e < a.K * a.K; e += blockDim.x) {
-    const int r = e / a.K, u = e % a.K;
-    const bool ok = (r < m && u < kb);
-    alpha_out[e] = ok ? MM::to(al[r * kb + u]) : 0.0;
-    beta_out[e] = ok ? MM::to(be[r * kb + u]) : 0.0;
+
+  // alpha[r][P_q] = Gamma[q][r], beta[r][P_r] = 1 (row stride K); the rest zero
+  for (int e = tid; e < a.K * a.K; e += 4 * NC) {
+    alpha_out[e] = 0.0;
+    beta_out[e] = 0.0;
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  for (int e = tid; e < m * m; e += 4 * NC) {
+    const int q = e / m, r = e % m;
+    alpha_out[r * a.K + s_P[q]] = MM::to(g[q * LD + r]);
+  }
+  for (int r = tid; r < m; r += 4 * NC) beta_out[r * a.K + s_P[r]] = 1.0;
+  if (tid == 0) {
     *accept_count = m;
+    if (failed) *status = 1;
     if (total) atomicAdd(total, (unsigned long long)m);
   }
+}
+
+template <int NC, typename T>
+static cudaError_t launch_metro_t(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
+                                  const uint8_t *forced, double *alpha, double *beta, int *accept_count,
+                                  int *status, unsigned long long *total, cudaStream_t st,
+                                  int reserve_smem) {
+  // reserve_smem > the block's own need claims that much shared memory so
+  // that no CTA of a concurrently running kernel shares the SM; the kernel's
+  // static shared memory (under 3 KB) comes on top
+  const size_t need = (size_t)2 * NC * (NC + 1) * sizeof(T);
+  size_t smem = need;
+  if ((size_t)reserve_smem > smem) smem = std::min<size_t>((size_t)reserve_smem, 224 * 1024);
+  const void *fn = (const void *)metropolis_block_kernel<NC, T>;
+  cudaError_t e = ensure_smem_attr(fn, (int)std::max<size_t>(smem, 200 * 1024));
+  if (e != cudaSuccess) return e;
+  DQ_KSCOPE(KF_METRO, st);
+  metropolis_block_kernel<NC, T><<<1, 4 * NC, smem, st>>>(a, g, g_f32 ? 1 : 0, s, forced, alpha, beta,
+                                                          accept_count, status, total);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_metropolis(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
@@ -231,22 +270,12 @@ cudaError_t launch_metropolis(const MetroArgs &a, const void *g, bool g_f32, int
                               int *status, unsigned long long *total, cudaStream_t st, bool df,
                               int reserve_smem) {
   if (a.kb < 1 || a.kb > 64 || a.kb > a.K) return cudaErrorInvalidValue;
-  // reserve_smem > the block's own need claims that much shared memory so
-  // that no CTA of a concurrently running kernel shares the SM
-  size_t smem = (size_t)(a.kb * (a.kb + 1) + 4 * a.kb * a.kb) * sizeof(double);
-  if ((size_t)reserve_smem > smem) smem = (size_t)reserve_smem;
-  const void *fn = df ? (const void *)metropolis_block_kernel<df64>
-                      : (const void *)metropolis_block_kernel<double>;
-  cudaError_t e = ensure_smem_attr(fn, (int)std::max<size_t>(smem, 5 * 64 * 65 * sizeof(double)));
-  if (e != cudaSuccess) return e;
-  DQ_KSCOPE(KF_METRO, st);
+  const bool wide = a.kb > 32;
   if (df)
-    metropolis_block_kernel<df64><<<1, 128, smem, st>>>(a, g, g_f32 ? 1 : 0, s, forced, alpha, beta,
-                                                        accept_count, status, total);
-  else
-    metropolis_block_kernel<double><<<1, 128, smem, st>>>(a, g, g_f32 ? 1 : 0, s, forced, alpha,
-                                                          beta, accept_count, status, total);
-  return cudaGetLastError();
+    return wide ? launch_metro_t<64, df64>(a, g, g_f32, s, forced, alpha, beta, accept_count, status, total, st, reserve_smem)
+                : launch_metro_t<32, df64>(a, g, g_f32, s, forced, alpha, beta, accept_count, status, total, st, reserve_smem);
+  return wide ? launch_metro_t<64, double>(a, g, g_f32, s, forced, alpha, beta, accept_count, status, total, st, reserve_smem)
+              : launch_metro_t<32, double>(a, g, g_f32, s, forced, alpha, beta, accept_count, status, total, st, reserve_smem);
 }
 
 // ----------------------------------------------------------------- A = G[:,S] alpha

@@ -49,10 +49,11 @@ def propagate(L, scale, side, X, Y=None, pre=None, post=None, vscale=None, df=Fa
     return Y
 
 
-def metropolis_block(N, site0, kb, g, s, lam, seed, chain, sweep_pass, slice1, forced=None):
-    """One delayed-update block (FP64): returns (alpha, beta, count, status) with
-    count a device int32 tensor (pass it to flush) -- alpha/beta rows < count
-    hold the coefficient vectors of the accepted flips."""
+def metropolis_block(N, site0, kb, g, s, lam, seed, chain, sweep_pass, slice1, forced=None, df=False):
+    """One delayed-update block (FP64, or double-float with df=True): returns
+    (alpha, beta, count, status) with count a device int32 tensor (pass it to
+    flush) -- alpha/beta rows < count hold the coefficient vectors of the
+    accepted flips."""
     import torch
     lib = _lib.load()
     _need(g, torch.float64, "g")
@@ -64,10 +65,11 @@ def metropolis_block(N, site0, kb, g, s, lam, seed, chain, sweep_pass, slice1, f
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     if forced is not None:
         forced = forced.to(device=dev, dtype=torch.uint8).contiguous()
-    check(lib.dqmc_op_metropolis_block(int(N), int(site0), int(kb), _ptr(g), int(g.shape[1]), _ptr(s),
-                                       float(lam), int(seed), int(chain), int(sweep_pass), int(slice1),
-                                       _ptr(forced), _ptr(alpha), _ptr(beta), _ptr(cnt), _ptr(st),
-                                       _stream(torch)))
+    fn = lib.dqmc_op_metropolis_block_df if df else lib.dqmc_op_metropolis_block
+    check(fn(int(N), int(site0), int(kb), _ptr(g), int(g.shape[1]), _ptr(s),
+             float(lam), int(seed), int(chain), int(sweep_pass), int(slice1),
+             _ptr(forced), _ptr(alpha), _ptr(beta), _ptr(cnt), _ptr(st),
+             _stream(torch)))
     return alpha, beta, cnt, int(st.item())
 
 
@@ -115,7 +117,7 @@ def trial_state(L, n_occ, eps=1e-4):
 def gemm(A, B, C=None, alpha=1.0, beta=0.0, ta=False, tb=False, mode="f64"):
     """C = alpha op(A) op(B) + beta C (FP64 tensors). mode: "f64" (FP64 FMA),
     "df" (double-float on the FP32 units), "oz" (exact digit slices on the bf16
-    tensor cores)."""
+    tensor cores, mma.sync), "tc" (the same digit slices on tcgen05)."""
     import torch
     lib = _lib.load()
     for t, n in ((A, "A"), (B, "B")):
@@ -126,7 +128,7 @@ def gemm(A, B, C=None, alpha=1.0, beta=0.0, ta=False, tb=False, mode="f64"):
     if C is None:
         C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
     _need(C, torch.float64, "C")
-    check(lib.dqmc_op_gemm_f64({"f64": 0, "df": 1, "oz": 2}[mode], int(ta), int(tb), M, N, K, float(alpha),
+    check(lib.dqmc_op_gemm_f64({"f64": 0, "df": 1, "oz": 2, "tc": 3}[mode], int(ta), int(tb), M, N, K, float(alpha),
                                _ptr(A), A.shape[1], _ptr(B), B.shape[1], float(beta), _ptr(C), C.shape[1],
                                _stream(torch)))
     return C

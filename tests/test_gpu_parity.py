@@ -137,7 +137,8 @@ def test_delayed_update_slice_matches_one_at_a_time(pkg, L, k, mode):
         Gcol = G[:, s0:s0 + kb].contiguous()
         Grow = G[s0:s0 + kb, :].contiguous()
         g = G[s0:s0 + kb, s0:s0 + kb].contiguous()
-        al, be, cnt, st = pkg.ops.metropolis_block(N, s0, kb, g, s, m.lam, seed, 0, 2 * sweep + pas, l)
+        al, be, cnt, st = pkg.ops.metropolis_block(N, s0, kb, g, s, m.lam, seed, 0, 2 * sweep + pas, l,
+                                                   df=(mode == "df"))
         assert st == 0
         pkg.ops.flush(N, s0, kb, G, Gcol, Grow, al, be, cnt, mode=mode)
     assert np.array_equal(s.cpu().numpy(), fref[l - 1])
@@ -454,7 +455,7 @@ def test_allocator_failure_reports_enomem(pkg):
 
 
 # ------------------------------------------------------------------ FP64-accurate GEMM variants
-@pytest.mark.parametrize("mode", ["f64", "df", "oz"])
+@pytest.mark.parametrize("mode", ["f64", "df", "oz", "tc"])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 def test_gemm_variants_are_fp64_accurate(pkg, mode, ta, tb):
     """FP64 FMA, double-float and tensor-core digit-slice GEMMs against numpy
@@ -473,14 +474,31 @@ def test_gemm_variants_are_fp64_accurate(pkg, mode, ta, tb):
     pkg.ops.gemm(dev(A), dev(B), C, alpha=0.7, beta=-0.3, ta=ta, tb=tb, mode=mode)
     bound = np.abs(opA) @ np.abs(opB) + np.abs(C0)
     rel = np.max(np.abs(C.cpu().numpy() - ref) / bound)
-    tol = {"f64": 1e-14, "df": 1e-13, "oz": 1e-14}[mode]
+    tol = {"f64": 1e-14, "df": 1e-13, "oz": 1e-14, "tc": 1e-14}[mode]
     assert rel < tol, rel
     # agreement with the FP64 FMA GEMM at the FP64 rounding level
     if mode != "f64":
         C64 = dev(C0)
         pkg.ops.gemm(dev(A), dev(B), C64, alpha=0.7, beta=-0.3, ta=ta, tb=tb, mode="f64")
         err = np.max(np.abs(C.cpu().numpy() - C64.cpu().numpy()) / bound)
-        assert err < {"df": 1e-13, "oz": 2e-15}[mode], err
+        assert err < {"df": 1e-13, "oz": 2e-15, "tc": 2e-15}[mode], err
+
+
+@pytest.mark.parametrize("M,N,K", [(1728, 1728, 1728), (64, 1664, 1664), (1, 1, 1), (129, 49, 65)])
+def test_tcgen05_digit_slice_gemm_matches_the_mma_sync_kernel(pkg, M, N, K):
+    """The tcgen05 digit-slice GEMM (tensor-memory accumulators) against the
+    mma.sync one on the stabilisation's shapes (square N^3 at L = 24, the
+    skinny QR trailing update, degenerate and ragged): the two sum the same
+    exact level sums, so they agree to the FP64 rounding of the final
+    combination."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    C1 = pkg.ops.gemm(dev(A), dev(B), mode="oz")
+    C2 = pkg.ops.gemm(dev(A), dev(B), mode="tc")
+    bound = np.abs(A) @ np.abs(B)
+    assert np.max(np.abs(C1.cpu().numpy() - C2.cpu().numpy()) / bound) < 1e-15
+    assert np.max(np.abs(C2.cpu().numpy() - A @ B) / bound) < 1e-14
 
 
 def test_digit_slice_gemm_accuracy_is_relative_to_row_scale(pkg):
