@@ -334,8 +334,8 @@ dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *G
                               const int *accept_count, void *stream);
 
 /* dqmc_op_flush_f64 without any device allocation. The paper has no
- * counterpart: this is a deployment variant of the Sec. II delayed-update
- * flush. Same arguments, semantics and FP64 result as dqmc_op_flush_f64, but
+ * counterpart: it is a deployment variant of dqmc_op_flush_f64 (above) for
+ * callers that cannot allocate. Same arguments, semantics and FP64 result, but
  * the N x K scratch for the factor A (K = kb rounded up to a power of two >= 4)
  * is a fixed device array compiled into the library: 248,832 doubles (1.9 MiB),
  * enough for N <= 3888 (L = 36) at K = 64. Larger N * K -> DQMC_EINVAL, before
@@ -344,8 +344,10 @@ dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *G
  * allocator up front (a cudaMallocAsync here could fail or grow a pool that
  * must stay fixed), and host code that must not block on the device
  * (cudaFree synchronises). The first call on a device resolves the array's
- * device address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture. Nothing has to start at zero: every
+ * device address (cudaGetSymbolAddress, with that device current) and keeps it
+ * for the life of the process; make that first call before any stream capture,
+ * and do not use the entry point on a device after cudaDeviceReset there (the
+ * kept address would belong to the destroyed context). Nothing has to start at zero: every
  * scratch entry is written before it is read. The one array is shared by all
  * calls on a device, so overlapping calls (several streams or host threads at
  * once) race; serialise them. */

@@ -24,7 +24,9 @@ constexpr size_t kNoAllocScratchDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxK;
 static __device__ __align__(256) double g_flush_scratch[kNoAllocScratchDoubles];
 
 // Device address of the scratch, resolved once per device with that device
-// current (the first call on a device does it).
+// current (the first call on a device does it) and kept for the process: a
+// cudaDeviceReset on that device would leave it pointing into the destroyed
+// context, so the entry point is not for use across a reset.
 static std::mutex g_scratch_mu;
 static std::vector<void *> g_scratch_addr;
 
