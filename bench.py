@@ -248,17 +248,29 @@ def gemm_microbench(n, mode, reps=5):
 
 def metro_microbench(L, k, df, reps=200):
     """One delayed-update block alone (decisions + Woodbury coefficients) on a
-    G-like block of the L x L torus, then the rank-k flush of that block."""
+    G-like block of the L x L torus, then the rank-k flush of that block:
+    device time per launch (CUDA events around `reps` back-to-back launches,
+    buffers allocated once)."""
+    import ctypes as C
+
     import torch
 
-    import paper_2608_03894_gb300 as pkg
     from dqmc_inputs import random_green_like
+    from paper_2608_03894_gb300 import _lib
+    lib = _lib.load()
     N = 3 * L * L
     G = torch.as_tensor(random_green_like(N, 1), dtype=torch.float64, device="cuda")
     s = torch.ones(N, dtype=torch.int8, device="cuda")
-    lam = 0.6538
     g = G[:k, :k].contiguous()
     Gcol, Grow = G[:, :k].contiguous(), G[:k, :].contiguous()
+    al = torch.zeros((k, k), dtype=torch.float64, device="cuda")
+    be = torch.zeros((k, k), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    P = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    metro = lib.dqmc_op_metropolis_block_df if df else lib.dqmc_op_metropolis_block
+    flush = lib.dqmc_op_flush_df if df else lib.dqmc_op_flush_f64
     res = {}
     for name in ("metropolis", "flush"):
         for i in range(reps + 5):
@@ -267,12 +279,13 @@ def metro_microbench(L, k, df, reps=200):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
             if name == "metropolis":
-                al, be, cnt, _ = pkg.ops.metropolis_block(N, 0, k, g, s, lam, 1, 0, i, 1, df=df)
+                _lib.check(metro(N, 0, k, P(g), k, P(s), 0.6538, 1, 0, i, 1, None, P(al), P(be), P(cnt), P(st), stream))
             else:
-                pkg.ops.flush(N, 0, k, G, Gcol, Grow, al, be, cnt, mode="df" if df else "f64")
+                _lib.check(flush(N, 0, k, P(G), P(Gcol), P(Grow), P(al), P(be), P(cnt), stream))
         e1.record()
         torch.cuda.synchronize()
         res[name + "_us"] = round(1000.0 * e0.elapsed_time(e1) / reps, 2)
+    res["accepted"] = int(cnt.item())
     return {"L": L, "k": k, "arith": "df" if df else "f64", **res}
 
 

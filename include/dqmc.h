@@ -147,6 +147,11 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                0 = FP64, whose serial chain is ~8x slower on this part);
  *   "stab_gemm"  stabilisation GEMMs: 0 = FP64, 1 = double-float, 2 = exact
  *                7-bit digit slices on the bf16 tensor cores (default 2);
+ *   "tc_gemm"    with stab_gemm = 2: 1 (default) = the digit-slice products
+ *                with M, N, K >= 256 on tcgen05 (tensor-memory accumulators),
+ *                the skinny ones on warp-level mma.sync; 0 = all on mma.sync;
+ *                a bounded wait of the tcgen05 kernel that gives up makes
+ *                dqmc_sweep return DQMC_ETIMEOUT;
  *   "gemm_sites" 32-bit mask of the stabilisation GEMM call sites that use the
  *                stab_gemm variant (default all);
  *   "gemm_df_sites" with stab_gemm = 2: mask of those sites that use the
@@ -378,6 +383,20 @@ dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, doub
  * n_occ-th and next level closer than 1e-9, or a pair k, -k split) or
  * 1 <= n_occ < N violated -> DQMC_EINVAL. */
 dqmc_status dqmc_op_trial_state(int L, int n_occ, double eps, double *P_out);
+
+/* Full-momentum maps of the two order-parameter correlators of Sec. III and
+ * IV from one FP64 G (N x N row-major, device, N = 3 L^2): for every mesh
+ * momentum Q = m1 b1 / L + m2 b2 / L, S_out[m1 * L + m2] = S_Pair(Q) (the
+ * symmetric pair structure factor, site positions R + tau_a when
+ * site_offsets != 0, else cell positions) and phi2_out[m1 * L + m2] =
+ * <phi^+ phi>(Q) (the CDW field with the sublattice phases 1, w, w^2, cell
+ * positions); the same definitions as dqmc_obs, at every Q. S_out and
+ * phi2_out: host arrays of L^2 doubles, caller-owned. One pass over G bins
+ * the correlations by sublattice pair and cell difference, then a Fourier
+ * sum per Q. Allocates its scratch on the stream and synchronises it.
+ * DQMC_EINVAL for an unsupported L or NULL pointers. */
+dqmc_status dqmc_op_measure_fullq(int L, const double *G, int site_offsets, double *S_out,
+                                  double *phi2_out, void *stream);
 
 /* Equal-time estimator sums from one FP64 G (N x N row-major, device): writes
  * out[6] (host) = S_pair_G, S_pair_dk, phi2_G, phi2_K, density, ekin, with the

@@ -71,6 +71,7 @@ SIGNATURES = {
     "dqmc_op_flush_f32": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_f64_noalloc": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_measure": (i32, [i32, vp, i32, vp, vp]),
+    "dqmc_op_measure_fullq": (i32, [i32, vp, i32, vp, vp, vp]),
     "dqmc_op_trial_state": (i32, [i32, i32, C.c_double, vp]),
     "dqmc_op_gemm_f64": (i32, [i32, i32, i32, i32, i32, i32, f64, vp, i32, vp, i32, f64, vp, i32, vp]),
 }

@@ -219,6 +219,7 @@ struct dqmc_ctx {
   int metro_reserve = 200 * 1024;  // shared memory the look-ahead Metropolis claims (own SM)
   int stab_gemm = 2;  // mixed: stabilisation GEMMs 0 FP64, 1 double-float, 2 tensor-core digit slices
   int stab_qr = 0;    // 0 Householder QR, 1 CholeskyQR2, -1 = CholeskyQR2 in mixed precision only
+  int tc_gemm = 1;    // mixed, digit slices: tcgen05 GEMM (else the mma.sync one)
   bool cholqr = false;  // the sweep's stabilisation uses CholeskyQR2 (resolved at allocation)
   unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
   unsigned gemm_df_sites = 0u;        // mixed: of those, the sites that use double-float products
@@ -735,6 +736,7 @@ struct GemmModeScope {
     } else if (c->stab_gemm == 2 && c->ozws) {
       set_oz_workspace(c->ozws, c->ozws_bytes, c->ozexp, 2 * (size_t)c->N);
       set_gemm_oz(true);
+      set_gemm_oz_tc(c->tc_gemm != 0);
       if (c->gemm_df_sites && c->dfws) {
         set_df_workspace(c->dfws, c->dfws_elems);
         set_gemm_df(true);
@@ -747,6 +749,7 @@ struct GemmModeScope {
     set_splitk_workspace(nullptr, 0);
     set_gemm_df(false);
     set_gemm_oz(false);
+    set_gemm_oz_tc(false);
     set_gemm_df_site_mask(0u);
   }
 };
@@ -942,6 +945,8 @@ dqmc_status read_status(dqmc_ctx *c) {
   c->accepted = (long)tot;
   c->last_drift = dm;
   c->max_drift = std::max(c->max_drift, dm);
+  if (c->precision == 1 && c->stab_gemm == 2 && c->tc_gemm && oz_tc_timed_out(c->stream))
+    return poison(c, fail(DQMC_ETIMEOUT, "a bounded wait of the tcgen05 GEMM gave up"));
   if (st[0] != 0) return fail(DQMC_ENUMERIC, "non-positive or non-finite acceptance ratio");
   if (st[1] != 0)
     return fail(DQMC_ENUMERIC, "non-positive pivot in the Cholesky factorisation of the CholeskyQR2 "
@@ -1040,6 +1045,8 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "stab_gemm must be 0, 1 or 2");
     c->stab_gemm = (int)v;
+  } else if (k == "tc_gemm") {
+    c->tc_gemm = v != 0.0;
   } else if (k == "stab_qr") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     if (v != 0.0 && v != 1.0 && v != -1.0) return fail(DQMC_EINVAL, "stab_qr must be -1 (auto), 0 or 1");

@@ -42,7 +42,7 @@ bool gemm_oz();
 // digit-slice products run on tcgen05 (tensor memory accumulators) instead of
 // the warp-level mma.sync kernel. oz_tc_timed_out: whether a bounded wait of
 // that kernel gave up since the library was loaded (synchronises the stream).
-void set_gemm_oz_tc(bool on);
+void set_gemm_oz_tc(bool on, bool force = false);  // force: every shape (else M, N, K >= 256)
 bool oz_tc_timed_out(cudaStream_t st);
 
 // Call sites of the stabilisation GEMMs. The fast FP64-accurate variants

@@ -217,7 +217,7 @@ dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, doub
     DQ_CUDA(cudaMallocAsync(&ws, bytes, st));
     DQ_CUDA(cudaMallocAsync((void **)&ex, ((size_t)M + N + 1) * sizeof(int), st));
     set_oz_workspace(ws, bytes, ex, (size_t)M + N + 1);
-    set_gemm_oz_tc(mode == 3);
+    set_gemm_oz_tc(mode == 3, true);
     e = ozgemm(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, nullptr, st);
     set_gemm_oz_tc(false);
     set_oz_workspace(nullptr, 0, nullptr, 0);

@@ -43,7 +43,8 @@ struct OzOperand {
   int rows, cols, ld, vec_is_row;
   int *emax;             // per vector: maximum exponent field
   int nvec, Kp;
-  unsigned short *out;   // digit planes [p][v][k]
+  unsigned short *out;   // digit planes [p][v][k], or with `blocked` [p][k / 16][v][k % 16]
+  int blocked;
 };
 
 // Both slicing passes work on tiles of 32 vectors x 64 positions along K,
@@ -138,7 +139,14 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand a, OzOperand b)
       F = sh >= 0 ? (m53 << sh) : (sh > -64 ? (m53 >> (-sh)) : 0ull);
     }
     const int neg = (int)(bits >> 63);
-    unsigned short *dst = o.out + (size_t)(v0 + v) * o.Kp + k0 + k;
+    const int kk = k0 + k, vv = v0 + v;
+    // blocked: [p][k / 16][v][16] with the two 8-position halves of a row
+    // swapped on rows 4..7 of every 8 (the 32-byte swizzle the tcgen05 kernel's
+    // descriptors expect, so that one bulk copy per plane lands ready)
+    unsigned short *dst = o.blocked
+                              ? o.out + ((size_t)(kk >> 4) * o.nvec + vv) * 16 +
+                                    ((((kk & 15) >> 3) ^ ((vv >> 2) & 1)) << 3) + (kk & 7)
+                              : o.out + (size_t)vv * o.Kp + kk;
 #pragma unroll
     for (int p = 1; p <= OZ_S; ++p) {
       int d = (int)((F >> (7 * OZ_S - 7 * p)) & 127ull);
@@ -333,59 +341,83 @@ __global__ void __launch_bounds__(256)
 // ====================================================================== tcgen05 path
 // The same digit-slice product on the 5th-generation tensor cores: bf16
 // tcgen05.mma (kind::f16, FP32 accumulate) with the accumulators in tensor
-// memory. CTA tile 128 x 48 (M x N), 128 threads. Thread 0 issues the MMAs;
-// all threads stage the operands with cp.async and fold the accumulators.
+// memory, fed from the digit planes the slicing kernel wrote.
 //
-// Shared memory: two stages of 32 positions of K, each holding the 9 digit
-// planes of the A tile (128 x 32 bf16) and of the B tile (48 x 32 bf16) in the
-// canonical K-major layout without swizzle: 8 x 16-byte core matrices, 128 B
-// each, the four along K adjacent (leading byte offset 128), 8-row groups
-// 512 B apart (stride byte offset). One K = 16 MMA reads two core-matrix
-// columns: the descriptor start advances by 256 B for the second half.
-//
+// CTA tile 128 x 48 (M x N), 192 threads, K in stages of 16 positions, four
+// stage buffers in shared memory: the 9 planes of the A tile (128 x 16 bf16)
+// and of the B tile (48 x 16), K-major with 32-byte rows in the 32-byte
+// swizzle (8-row groups of 256 B: stride byte offset 256). The slicing kernel
+// writes the planes blocked by 16 positions of K and already swizzled, so a
+// plane's rows of one stage are one contiguous run that a single bulk copy
+// (cp.async.bulk, completing on the slot's mbarrier by byte count) moves.
+// One thread issues the copies up to four stages ahead; another issues the
+// 45 MMAs of a stage (digit pairs p + q <= 10) as soon as its copies have
+// landed; a slot is refilled once the MMAs that read it have completed
+// (tcgen05.commit on one mbarrier per slot).
 // Tensor memory: 512 columns; level l = p + q (2..10) accumulates in columns
-// 48 (l - 2) .. 48 (l - 2) + 47, lane = output row. Every 64 positions of K
-// (two stages) the sums of levels 2..6 are exact integers below 2^24; all
-// threads wait for the MMAs (mbarrier of tcgen05.commit), load their row of
-// those levels (tcgen05.ld 32x32b, lanes 32 w .. 32 w + 31 for warp w) and
-// fold them into an exact int64 accumulator (weights 2^{7(6-l)}); the next
-// period's first MMA of each of these levels overwrites (enable-input-d
-// false). Levels 7..10 keep accumulating in FP32 over the whole K: their
-// rounding stays below 2^-53 of the level-2 sum, and they are read once.
+// 48 (l - 2) .. 48 (l - 2) + 47, lane = output row. Every 128 positions of K
+// (eight stages) the sums of levels 2..6 are exact integers below 2^24 (a
+// level has at most 5 digit pairs: 5 * 128 * 127^2 < 2^24); all threads wait
+// for the MMAs, load their row of those levels (tcgen05.ld 32x32b: warps w
+// and w + 4 read lanes 32 (w % 4) .. + 31, columns 0..23 and 24..47) and
+// fold them into an exact int64 accumulator
+// (weights 2^{7(6-l)}); the next period's first MMA of each of these levels
+// overwrites (enable-input-d false). Levels 7..10 keep accumulating in FP32
+// over the whole K (their rounding stays below 2^-53 of the level-2 sum) and
+// are read once. Measured on this part: an M128 x N48 x K16 bf16 MMA issues
+// every 46 cycles (N = 256: 128 cycles, 2.4 PFLOP/s over the 152 SMs).
 //
 // Every wait on an mbarrier is bounded; a wait that gives up sets a device
 // flag (read by oz_tc_timed_out) and the CTA stops issuing work, drains its
 // copies, frees its tensor memory and returns.
-constexpr int TC_BM = 128, TC_BN = 48, TC_BK = 32;
-constexpr int TC_A_PLANE = TC_BM * TC_BK * 2;                 // bytes
-constexpr int TC_B_PLANE = TC_BN * TC_BK * 2;
-constexpr int TC_STAGE = OZ_S * (TC_A_PLANE + TC_B_PLANE);    // 101376 B
-constexpr int TC_SMEM = 2 * TC_STAGE + 128;                   // + mbarriers and the TMEM address
+constexpr int TC_BM = 128, TC_BN = 48, TC_BK = 16, TC_NS = 4;
+constexpr int TC_A_PLANE = TC_BM * TC_BK * 2, TC_B_PLANE = TC_BN * TC_BK * 2;
+constexpr int TC_DIG = OZ_S * (TC_A_PLANE + TC_B_PLANE);                 // 50688 B per stage
+constexpr int TC_SMEM = TC_NS * TC_DIG + 128;                            // + mbarriers, TMEM address, abort flag
 constexpr int TC_TMEM_COLS = 512;
 constexpr uint32_t TC_IDESC = (1u << 4)                       // D: FP32
                               | (1u << 7) | (1u << 10)        // A, B: bf16
                               | ((uint32_t)(TC_BN >> 3) << 17)  // N >> 3
                               | ((uint32_t)(TC_BM >> 4) << 24); // M >> 4; both operands K-major
-constexpr int TC_WAIT_LIMIT = 1 << 22;
+constexpr int TC_WAIT_LIMIT = 1 << 26;  // polls (~0.1-1 s)
+constexpr int TC_FOLD = 8;  // stages per fold of the exact levels (128 positions)
 
 __device__ int g_oz_tc_timeout = 0;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
-// shared-memory matrix descriptor: start, LBO 128 B, SBO 512 B, no swizzle
+// shared-memory matrix descriptor of a K-major tile with 32-byte rows (16
+// bf16 positions) in the 32-byte swizzle: start, leading byte offset 16
+// (unused: one K = 16 step is the whole row), stride byte offset 256 (8-row
+// groups), version 1, layout type 6
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
-         ((uint64_t)(512 >> 4) << 32) | (1ull << 46);
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(16 >> 4) << 16) |
+         ((uint64_t)(256 >> 4) << 32) | (1ull << 46) | (6ull << 61);
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, int bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes));
 }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+// Spin on the phase with the non-blocking test (try_wait may suspend the
+// thread for a system-dependent time, which here would add its wake-up
+// latency to every stage); bounded.
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+        "{\n .reg .pred P;\n mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
         : "=r"(ok)
         : "r"(addr), "r"(parity)
         : "memory");
@@ -403,66 +435,110 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
                : "memory");
 }
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+// 8 columns of this warp's 32 lanes into v[0..7]; the caller waits
+__device__ __forceinline__ void tc_ld8_nowait(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+// 16 columns of this warp's 32 lanes into v[0..15]; the caller waits (tcgen05.wait::ld)
+__device__ __forceinline__ void tc_ld16_nowait(uint32_t taddr, float *v) {
   uint32_t r[16];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Stage `st` (positions k0 .. k0 + 31) into buffer b: every thread copies
-// 16-byte pieces (8 positions of one row of one plane); rows beyond M / N
-// are zero-filled.
-__device__ __forceinline__ void tc_stage(uint32_t sbase, int b, const unsigned short *Ad,
-                                         const unsigned short *Bd, int M, int N, int Kp, int m0,
-                                         int n0, int k0, size_t aplane, size_t bplane) {
-  constexpr int ROWS = TC_BM + TC_BN, PER_PLANE = ROWS * (TC_BK / 8);
-  const uint32_t stage = sbase + b * TC_STAGE;
-  for (int e = threadIdx.x; e < OZ_S * PER_PLANE; e += blockDim.x) {
-    const int p = e / PER_PLANE, rem = e % PER_PLANE;
-    const int r = rem >> 2, kg = rem & 3;
-    uint32_t dst;
-    const unsigned short *src;
-    int ok;
-    if (r < TC_BM) {
-      dst = stage + p * TC_A_PLANE + (((r >> 3) * 4 + kg) << 7) + ((r & 7) << 4);
-      ok = (m0 + r) < M;
-      src = Ad + p * aplane + (size_t)(ok ? m0 + r : 0) * Kp + k0 + kg * 8;
-    } else {
-      const int rb = r - TC_BM;
-      dst = stage + OZ_S * TC_A_PLANE + p * TC_B_PLANE + (((rb >> 3) * 4 + kg) << 7) + ((rb & 7) << 4);
-      ok = (n0 + rb) < N;
-      src = Bd + p * bplane + (size_t)(ok ? n0 + rb : 0) * Kp + k0 + kg * 8;
-    }
-    cp_async16_zfill(dst, src, ok ? 16 : 0);
+// Stage `st` (positions k0 .. k0 + 15) of the digit planes into slot b by one
+// thread: per plane, the 128 rows of the A tile and the 48 of the B tile are
+// contiguous 32-byte rows of the blocked plane layout (already in the 32-byte
+// swizzle), two bulk copies (cp.async.bulk) completing on the slot's mbarrier
+// with the byte count. Rows beyond M / N are not copied: the slot keeps stale
+// rows there, which feed only output rows / columns that are never stored.
+__device__ __forceinline__ uint32_t tc_stage_bytes(int M, int N, int m0, int n0) {
+  const int ra = min(TC_BM, M - m0), rb = min(TC_BN, N - n0);
+  return (uint32_t)(OZ_S * (ra + rb) * 32);
+}
+__device__ __forceinline__ void tc_stage_bulk(uint32_t sdig, int b, uint32_t mbar, const unsigned short *Ad,
+                                              const unsigned short *Bd, int M, int N, int m0, int n0, int k0,
+                                              size_t aplane, size_t bplane) {
+  const int ra = min(TC_BM, M - m0), rb = min(TC_BN, N - n0);
+  const uint32_t stage = sdig + b * TC_DIG;
+  const size_t kb = (size_t)(k0 >> 4);
+  mbar_expect_tx(mbar, tc_stage_bytes(M, N, m0, n0));
+#pragma unroll 1
+  for (int p = 0; p < OZ_S; ++p) {
+    bulk_copy(stage + p * TC_A_PLANE, Ad + p * aplane + (kb * M + m0) * 16, (uint32_t)ra * 32, mbar);
+    bulk_copy(stage + OZ_S * TC_A_PLANE + p * TC_B_PLANE, Bd + p * bplane + (kb * N + n0) * 16, (uint32_t)rb * 32,
+              mbar);
   }
-  cp_async_commit();
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Warp roles (192 threads): warps 0-3 fold and write the output (TMEM lane
+// quarters 0-3), warp 4 lane 0 issues the MMAs, warp 5 lane 0 the bulk
+// copies. They hand over through mbarriers only, never a CTA-wide barrier
+// inside the K loop, so the MMA thread (which blocks while the tensor pipe's
+// queue is full) never holds up the copies:
+//   full[b]  (expect_tx)      the bulk copies of the stage in slot b landed
+//   empty[b] (tcgen05.commit) the MMAs that read slot b completed
+//   acc      (tcgen05.commit) the MMAs up to a fold point completed
+//   freed    (4 arrivals)     one per fold warp, after its tensor-memory loads
+constexpr int TC_THREADS = 192;
+constexpr int TC_COPY0 = 160;  // the copy thread (warp 5, lane 0)
+
+// Bounded phase wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t addr, uint32_t parity, volatile int *abort) {
+  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 1023) == 1023 && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(addr) : "memory");
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
     oz_gemm_tc_kernel(int M, int N, int Kp, const unsigned short *__restrict__ Ad,
                       const unsigned short *__restrict__ Bd, const int *__restrict__ ea,
                       const int *__restrict__ eb, double alpha, double beta, double *__restrict__ C,
                       int ldc, const double *__restrict__ rs, const double *__restrict__ cs,
-                      int kchunks, double *__restrict__ part) {
+                      int kstages, double *__restrict__ part) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
   const size_t aplane = (size_t)M * Kp, bplane = (size_t)N * Kp;
-  const uint32_t sbase = smem_u32(tsm);
-  unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tsm + 2 * TC_STAGE);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(tsm + 2 * TC_STAGE + 64);
-  const uint32_t mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
+  const uint32_t sdig = smem_u32(tsm);
+  // mbarriers: full[4], empty[4], acc, freed; then the TMEM address and the abort flag
+  unsigned char *ctl = tsm + TC_NS * TC_DIG;
+  const uint32_t mb = smem_u32(ctl);
+  const uint32_t mb_full = mb, mb_empty = mb + 8 * TC_NS, mb_acc = mb + 16 * TC_NS, mb_freed = mb_acc + 8;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(ctl + 16 * TC_NS + 16);
+  volatile int *abort = reinterpret_cast<volatile int *>(ctl + 16 * TC_NS + 20);
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb1));
+    for (int bb = 0; bb < TC_NS; ++bb) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_full + 8 * bb));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_empty + 8 * bb));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb_acc));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(mb_freed));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    *abort = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
@@ -474,142 +550,150 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tbase = *tslot;
 
-  long long I[TC_BN];
-#pragma unroll
-  for (int c = 0; c < TC_BN; ++c) I[c] = 0;
+  // split K: this CTA takes stages [z kstages, (z + 1) kstages) of 16 positions
+  const int sbeg = blockIdx.z * kstages;
+  const int nst = max(0, min(Kp / TC_BK, sbeg + kstages) - sbeg);
+  const int nfold = (nst + TC_FOLD - 1) / TC_FOLD;
 
-  const int kbeg = blockIdx.z * kchunks * OZ_KC;
-  const int kend = min(Kp, kbeg + kchunks * OZ_KC);
-  const int nst = (kend - kbeg) / TC_BK;  // even: Kp and the chunk bounds are multiples of 64
-  bool bad = false;
-  if (nst > 0) tc_stage(sbase, 0, Ad, Bd, M, N, Kp, m0, n0, kbeg, aplane, bplane);
-  for (int st = 0; st < nst && !bad; ++st) {
-    const int b = st & 1;
-    if (st + 1 < nst) {
-      // buffer b ^ 1 last fed the MMAs of stage st - 1: wait for them first
-      bool ok = true;
-      if (st >= 1) ok = mbar_wait(b ? mb0 : mb1, ((st - 1) >> 1) & 1);
-      if (__syncthreads_or(!ok)) {
-        bad = true;
-        break;
-      }
-      tc_stage(sbase, b ^ 1, Ad, Bd, M, N, Kp, m0, n0, kbeg + (st + 1) * TC_BK, aplane, bplane);
-      cp_async_wait_one();
-    } else {
-      cp_async_wait_all();
+  if (tid == TC_COPY0) {
+    // ---- copier: stage st into slot st % 4 once the MMAs of stage st - 4 are done
+    for (int st = 0; st < nst; ++st) {
+      const int b = st % TC_NS;
+      if (st >= TC_NS && !mbar_wait_or_abort(mb_empty + 8 * b, ((st / TC_NS) - 1) & 1, abort)) break;
+      tc_stage_bulk(sdig, b, mb_full + 8 * b, Ad, Bd, M, N, m0, n0, (sbeg + st) * TC_BK, aplane, bplane);
     }
-    // the copies become visible to the tensor core (async proxy), then to thread 0
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (tid == 128) {
+    // ---- MMA issuer
+    for (int st = 0; st < nst; ++st) {
+      const int b = st % TC_NS;
+      if (!mbar_wait_or_abort(mb_full + 8 * b, (st / TC_NS) & 1, abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t abase = sbase + b * TC_STAGE, bbase = abase + OZ_S * TC_A_PLANE;
-      const bool first = (st & 1) == 0;
+      const uint64_t ad0 = tc_desc(sdig + b * TC_DIG), bd0 = tc_desc(sdig + b * TC_DIG + OZ_S * TC_A_PLANE);
+      // a new fold period overwrites the exact levels: the previous fold must have read them
+      const bool restart = (st % TC_FOLD) == 0;
+      if (st > 0 && restart) {
+        if (!mbar_wait_or_abort(mb_freed, ((st / TC_FOLD) - 1) & 1, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      }
+      // exact levels 2..6 restart every TC_FOLD stages, 7..10 only at the first
 #pragma unroll 1
-      for (int kk = 0; kk < TC_BK / 16; ++kk) {
+      for (int p = 0; p < OZ_S; ++p)
 #pragma unroll 1
-        for (int p = 0; p < OZ_S; ++p) {
-          const uint64_t ad = tc_desc(abase + p * TC_A_PLANE + kk * 256);
-#pragma unroll 1
-          for (int q = 0; p + q <= OZ_S - 1; ++q) {
-            const uint64_t bd = tc_desc(bbase + q * TC_B_PLANE + kk * 256);
-            // levels 2..6 restart every 64 positions, 7..10 only at the first
-            const uint32_t acc = (first && kk == 0 && p == 0 && (q <= 4 || st == 0)) ? 0u : 1u;
-            tc_mma(tbase + (uint32_t)((p + q) * TC_BN), ad, bd, acc);
-          }
+        for (int q = 0; p + q <= OZ_S - 1; ++q) {
+          const uint32_t accf = (restart && p == 0 && (q <= 4 || st == 0)) ? 0u : 1u;
+          tc_mma(tbase + (uint32_t)((p + q) * TC_BN), ad0 + (uint64_t)((p * TC_A_PLANE) >> 4),
+                 bd0 + (uint64_t)((q * TC_B_PLANE) >> 4), accf);
         }
-      }
-      tc_commit(b ? mb1 : mb0);
+      tc_commit(mb_empty + 8 * b);
+      if ((st % TC_FOLD) == TC_FOLD - 1 || st == nst - 1) tc_commit(mb_acc);
     }
-    if (st & 1) {
-      // end of 64 positions: fold the exact level sums
-      const bool ok = mbar_wait(b ? mb1 : mb0, (st >> 1) & 1);
-      if (__syncthreads_or(!ok)) {
-        bad = true;
-        break;
-      }
+  }
+
+  // ---- folds and output: warps 0-3, lane quarter = warp
+  const int i = m0 + warp * 32 + lane;
+  if (warp < 4) {
+    long long I[TC_BN];
+#pragma unroll
+    for (int c = 0; c < TC_BN; ++c) I[c] = 0;
+    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+    bool ok = true;
+    for (int f = 0; f < nfold && ok; ++f) {
+      // lane 0 polls and the warp follows its verdict, so the aligned
+      // tensor-memory loads stay warp-uniform
+      int okw = lane == 0 ? (int)mbar_wait_or_abort(mb_acc, f & 1, abort) : 0;
+      ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
+      if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
       for (int idx = 0; idx < 5; ++idx) {
         const int l = idx + 2;
 #pragma unroll
         for (int ch = 0; ch < TC_BN / 16; ++ch) {
           float v[16];
-          tc_ld16(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
+          tc_ld16_nowait(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-          for (int i = 0; i < 16; ++i) I[ch * 16 + i] += ((long long)__float2int_rn(v[i])) << (7 * (6 - l));
+          for (int c = 0; c < 16; ++c) I[ch * 16 + c] += ((long long)__float2int_rn(v[c])) << (7 * (6 - l));
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncthreads();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(mb_freed);
     }
-  }
-  if (bad) {
-    if (tid == 0) atomicExch(&g_oz_tc_timeout, 1);
-    cp_async_wait_all();
-  }
-  // levels 7..10 (weights 2^{-7(l-6)}) are read once, 16 columns at a time
-  // (the last period's fold waited for every MMA), and the outputs of those
-  // columns are formed: (I + F) 2^{-42} 2^{E_i + F_j}
-  const int i = m0 + warp * 32 + lane;
-  const bool row_ok = !bad && nst > 0 && i < M;
-  const double r = (rs && i < M) ? rs[i] * alpha : alpha;
-  if (!bad && nst > 0) {
-    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+    // levels 7..10 (weights 2^{-7(l-6)}) are read once, 16 columns at a time
+    // (the last fold waited for every MMA), and the outputs formed:
+    // (I + F) 2^{-42} 2^{E_i + F_j}
+    if (ok && nst > 0) {
+      const bool row_ok = i < M;
+      const double r = (rs && row_ok) ? rs[i] * alpha : alpha;
 #pragma unroll
-    for (int ch = 0; ch < TC_BN / 16; ++ch) {
-      float F[16];
+      for (int ch = 0; ch < TC_BN / 16; ++ch) {
+        float F[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) F[c] = 0.f;
+        for (int c = 0; c < 16; ++c) F[c] = 0.f;
 #pragma unroll
-      for (int idx = 5; idx < OZ_S; ++idx) {
-        const float w = __int_as_float((127 - 7 * (idx - 4)) << 23);
-        float v[16];
-        tc_ld16(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
+        for (int idx = 5; idx < OZ_S; ++idx) {
+          const float w = __int_as_float((127 - 7 * (idx - 4)) << 23);
+          float v[16];
+          tc_ld16_nowait(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 16; ++c) F[c] = fmaf(v[c], w, F[c]);
-      }
-      if (row_ok) {
+          for (int c = 0; c < 16; ++c) F[c] = fmaf(v[c], w, F[c]);
+        }
+        if (row_ok) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int j = n0 + ch * 16 + c;
-          if (j >= N) continue;
-          const double dot = (double)I[ch * 16 + c] + (double)F[c];
-          const int e2 = (ea[i] - 1022) + (eb[j] - 1022) - 42;
-          double v = ldexp(dot, e2) * r;
-          if (cs) v *= cs[j];
-          double *cp = C + (size_t)i * ldc + j;
-          if (part)
-            part[((size_t)blockIdx.z * M + i) * N + j] = v;
-          else
-            *cp = (beta != 0.0) ? v + beta * (*cp) : v;
+          for (int c = 0; c < 16; ++c) {
+            const int j = n0 + ch * 16 + c;
+            if (j >= N) continue;
+            const double dot = (double)I[ch * 16 + c] + (double)F[c];
+            const int e2 = (ea[i] - 1022) + (eb[j] - 1022) - 42;
+            double v = ldexp(dot, e2) * r;
+            if (cs) v *= cs[j];
+            double *cp = C + (size_t)i * ldc + j;
+            if (part)
+              part[((size_t)blockIdx.z * M + i) * N + j] = v;
+            else
+              *cp = (beta != 0.0) ? v + beta * (*cp) : v;
+          }
         }
       }
+    } else if (!*abort && nst == 0 && i < M) {
+      // an empty K range: the product is zero
+      for (int c = 0; c < TC_BN; ++c) {
+        const int j = n0 + c;
+        if (j >= N) break;
+        double *cp = C + (size_t)i * ldc + j;
+        if (part)
+          part[((size_t)blockIdx.z * M + i) * N + j] = 0.0;
+        else
+          *cp = (beta != 0.0) ? beta * (*cp) : 0.0;
+      }
     }
   }
+  cp_async_wait_n<0>();
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-  __syncthreads();
+  if (__syncthreads_or(*abort)) {
+    // give the MMAs already issued a bounded time to finish before the tensor memory goes
+    if (tid == 128) {
+      volatile int *never = abort + 1;  // a flag nothing sets: the drain runs to its own limit
+      *never = 0;
+      tc_commit(mb_acc);
+      mbar_wait_or_abort(mb_acc, nfold & 1, never);
+      atomicExch(&g_oz_tc_timeout, 1);
+    }
+    __syncthreads();
+  }
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TC_TMEM_COLS));
   }
-  if (!bad && nst == 0 && i < M) {
-    // an empty K range: the product is zero
-    for (int c = 0; c < TC_BN; ++c) {
-      const int j = n0 + c;
-      if (j >= N) break;
-      double *cp = C + (size_t)i * ldc + j;
-      if (part)
-        part[((size_t)blockIdx.z * M + i) * N + j] = 0.0;
-      else
-        *cp = (beta != 0.0) ? beta * (*cp) : 0.0;
-    }
-  }
 }
 
-static thread_local bool t_oz_tc = false;
-void set_gemm_oz_tc(bool on) { t_oz_tc = on; }
+static thread_local bool t_oz_tc = false, t_oz_tc_force = false;
+void set_gemm_oz_tc(bool on, bool force) {
+  t_oz_tc = on;
+  t_oz_tc_force = on && force;
+}
 
 bool oz_tc_timed_out(cudaStream_t st) {
   int v = 0;
@@ -654,8 +738,13 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
   if (e != cudaSuccess) return e;
   // op(A) rows: storage rows when !ta (M x K), storage columns when ta (K x M);
   // op(B) columns: storage columns when !tb (K x N), storage rows when tb (N x K)
-  const OzOperand oa{A, ta ? K : M, ta ? M : K, lda, ta ? 0 : 1, ea, M, Kp, Ad};
-  const OzOperand ob{B, tb ? N : K, tb ? K : N, ldb, tb ? 1 : 0, eb, N, Kp, Bd};
+  // the tcgen05 kernel reads the planes blocked by 16 positions of K: one
+  // stage of one plane is then a contiguous run of 16-position rows
+  // tcgen05 tiles are 128 x 48: the skinny products of the QR panels (64
+  // rows) run faster on the mma.sync kernel's 64 x 64 tiles
+  const bool tc = t_oz_tc && (t_oz_tc_force || (M >= 256 && N >= 256 && K >= 256));
+  const OzOperand oa{A, ta ? K : M, ta ? M : K, lda, ta ? 0 : 1, ea, M, Kp, Ad, tc ? 1 : 0};
+  const OzOperand ob{B, tb ? N : K, tb ? K : N, ldb, tb ? 1 : 0, eb, N, Kp, Bd, tc ? 1 : 0};
   const int stiles = ((M + OZ_TV - 1) / OZ_TV + (N + OZ_TV - 1) / OZ_TV) * (Kp / OZ_TK);
   {
     DQ_KSCOPE(KF_SLICE, st);
@@ -665,13 +754,13 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
     DQ_KSCOPE(KF_SLICE, st);
     oz_slice_kernel<<<stiles, 256, 0, st>>>(oa, ob);
   }
-  const bool tc = t_oz_tc;
   const int BM = tc ? TC_BM : OZ_BM, BN = tc ? TC_BN : OZ_BN;
   const int smem = tc ? TC_SMEM : 2 * OZ_BUF * (int)sizeof(unsigned short);  // two staging buffers
   e = ensure_smem_attr(tc ? (const void *)oz_gemm_tc_kernel : (const void *)oz_gemm_rb_kernel, smem);
   if (e != cudaSuccess) return e;
   // one CTA per SM (shared memory); split K when the tiles do not fill the GPU
   const int tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  // K is split in chunks of 64 positions (the tcgen05 kernel counts stages of 16)
   const int nchunks = Kp / OZ_KC;
   int splits = 1;
   if (tiles < 152) {
@@ -692,8 +781,8 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
   add_work(KF_GEMM, 2.0 * M * (double)N * K,
            8.0 * ((double)M * K + (double)K * N + (beta != 0.0 ? 2.0 : 1.0) * (double)M * N));
   if (tc)
-    oz_gemm_tc_kernel<<<grid, 128, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
-                                              kchunks, part);
+    oz_gemm_tc_kernel<<<grid, TC_THREADS, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
+                                              kchunks * (OZ_KC / TC_BK), part);
   else
     oz_gemm_rb_kernel<<<grid, 256, smem, st>>>(M, N, Kp, Ad, Bd, ea, eb, alpha, beta, C, ldc, rs, cs,
                                               kchunks, part);

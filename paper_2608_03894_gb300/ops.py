@@ -103,6 +103,20 @@ def measure(L, G, site_offsets=True):
     return dict(zip(("S_pair_G", "S_pair_dk", "phi2_G", "phi2_K", "density", "ekin"), out.tolist()))
 
 
+def measure_fullq(L, G, site_offsets=True):
+    """S_Pair(Q) and <phi^+ phi>(Q) at every mesh momentum (two L x L numpy
+    arrays indexed [m1, m2]) from one FP64 G."""
+    import numpy as np
+    import torch
+    lib = _lib.load()
+    _need(G, torch.float64, "G")
+    S = np.zeros((L, L))
+    P = np.zeros((L, L))
+    check(lib.dqmc_op_measure_fullq(int(L), _ptr(G), int(bool(site_offsets)), S.ctypes.data_as(C.c_void_p),
+                                    P.ctypes.data_as(C.c_void_p), _stream(torch)))
+    return S, P
+
+
 def trial_state(L, n_occ, eps=1e-4):
     """Projector-QMC trial orbitals: N x n_occ orthonormal real basis of the
     lowest n_occ eigenstates of K + eps diag(+1, 0, -1) (host numpy array)."""

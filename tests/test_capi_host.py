@@ -74,6 +74,13 @@ def test_create_and_destroy_without_gpu_work(lib):
     assert lib.dqmc_set_option(h, b"n_stab", 0.0) == 1
     assert lib.dqmc_set_option(h, b"drift_limit", -1.0) == 1
     assert lib.dqmc_set_option(h, None, 1.0) == 1
+    # options of the stabilisation and the Metropolis block
+    assert lib.dqmc_set_option(h, b"stab_qr", 1.0) == 0
+    assert lib.dqmc_set_option(h, b"stab_qr", -1.0) == 0
+    assert lib.dqmc_set_option(h, b"stab_qr", 2.0) == 1
+    assert lib.dqmc_set_option(h, b"tc_gemm", 0.0) == 0
+    assert lib.dqmc_set_option(h, b"df_metro", 0.0) == 0
+    assert lib.dqmc_set_option(h, b"metro_reserve", 224 * 1024 + 1.0) == 1
     lib.dqmc_destroy(h)
 
 

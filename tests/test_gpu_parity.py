@@ -189,6 +189,26 @@ def test_measure_matches_wick_estimators(pkg, L, offsets):
 
 
 # ------------------------------------------------------------------ whole context
+@pytest.mark.parametrize("L,offsets", [(1, True), (2, True), (3, True), (3, False), (4, True), (6, False),
+                                       (12, True)])
+def test_full_momentum_maps_match_the_oracle(pkg, L, offsets):
+    """S_Pair(Q) and <phi^+ phi>(Q) at every mesh momentum (Sec. III, IV)
+    against the oracle's maps, each Q by its definition, on a G-like matrix;
+    at Gamma, Gamma + dk and K they also equal the single-momentum kernel."""
+    N = 3 * L * L
+    G0 = random_green_like(N, 13 + L)
+    S, P = pkg.ops.measure_fullq(L, dev(G0), site_offsets=offsets)
+    Sref = omeas.pair_structure_factor_all(G0, L, site_offsets=offsets)
+    Pref = omeas.cdw_correlator_all(G0, L)
+    assert np.max(np.abs(S - Sref)) < 1e-12 * max(1.0, np.max(np.abs(Sref)))
+    assert np.max(np.abs(P - Pref)) < 1e-12 * max(1.0, np.max(np.abs(Pref)))
+    single = pkg.ops.measure(L, dev(G0), site_offsets=offsets)
+    assert abs(S[0, 0] - single["S_pair_G"]) < 1e-12 and abs(P[0, 0] - single["phi2_G"]) < 1e-12
+    assert abs(S[1 % L, 0] - single["S_pair_dk"]) < 1e-12
+    if L % 3 == 0:
+        assert abs(P[L // 3, 2 * L // 3] - single["phi2_K"]) < 1e-12
+
+
 def test_green_from_scratch_fixed_field_L4(pkg):
     par = dict(L=4, beta=2.0, dtau=0.1, U=-4.0, mu=-1.0)
     m = omodel.Model(**par)
@@ -484,21 +504,28 @@ def test_gemm_variants_are_fp64_accurate(pkg, mode, ta, tb):
         assert err < {"df": 1e-13, "oz": 2e-15, "tc": 2e-15}[mode], err
 
 
-@pytest.mark.parametrize("M,N,K", [(1728, 1728, 1728), (64, 1664, 1664), (1, 1, 1), (129, 49, 65)])
-def test_tcgen05_digit_slice_gemm_matches_the_mma_sync_kernel(pkg, M, N, K):
-    """The tcgen05 digit-slice GEMM (tensor-memory accumulators) against the
-    mma.sync one on the stabilisation's shapes (square N^3 at L = 24, the
-    skinny QR trailing update, degenerate and ragged): the two sum the same
-    exact level sums, so they agree to the FP64 rounding of the final
-    combination."""
+@pytest.mark.parametrize("M,N,K", [(1728, 1728, 1728), (64, 1664, 1664), (2, 2, 2), (130, 50, 66),
+                                   (129, 49, 65)])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, True), (True, False), (False, True)])
+def test_tcgen05_digit_slice_gemm_matches_the_mma_sync_kernel(pkg, M, N, K, ta, tb):
+    """The tcgen05 digit-slice GEMM (slicing fused into its producer, tensor-
+    memory accumulators) against the mma.sync one on the stabilisation's
+    shapes (square N^3 at L = 24, the skinny QR trailing update, degenerate,
+    ragged against every tile and stage; odd leading dimensions take the
+    mma.sync path), in every transpose combination: the two sum the same exact
+    level sums, so they agree to the FP64 rounding of the final combination."""
     rng = np.random.default_rng(11)
-    A = rng.standard_normal((M, K))
-    B = rng.standard_normal((K, N))
-    C1 = pkg.ops.gemm(dev(A), dev(B), mode="oz")
-    C2 = pkg.ops.gemm(dev(A), dev(B), mode="tc")
-    bound = np.abs(A) @ np.abs(B)
+    opA = rng.standard_normal((M, K)) * np.exp2(rng.integers(-20, 20, size=(M, 1)))
+    opB = rng.standard_normal((K, N)) * np.exp2(rng.integers(-20, 20, size=(1, N)))
+    A = np.ascontiguousarray(opA.T) if ta else opA
+    B = np.ascontiguousarray(opB.T) if tb else opB
+    C0 = rng.standard_normal((M, N))
+    C1, C2 = dev(C0), dev(C0)
+    pkg.ops.gemm(dev(A), dev(B), C1, alpha=0.7, beta=-0.3, ta=ta, tb=tb, mode="oz")
+    pkg.ops.gemm(dev(A), dev(B), C2, alpha=0.7, beta=-0.3, ta=ta, tb=tb, mode="tc")
+    bound = np.abs(opA) @ np.abs(opB) + np.abs(C0)
     assert np.max(np.abs(C1.cpu().numpy() - C2.cpu().numpy()) / bound) < 1e-15
-    assert np.max(np.abs(C2.cpu().numpy() - A @ B) / bound) < 1e-14
+    assert np.max(np.abs(C2.cpu().numpy() - (0.7 * opA @ opB - 0.3 * C0)) / bound) < 1e-14
 
 
 def test_digit_slice_gemm_accuracy_is_relative_to_row_scale(pkg):
