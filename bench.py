@@ -451,6 +451,11 @@ def run_ours(args, rank, world, local_rank):
             roof = {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops_sustained", 1700.0),
                     "unit": "TFLOP/s", "peak_source": f"{peak_src} sustained bf16 (cuBLAS); bf16 MMA rate of the "
                                                        "digit-slice GEMM = 45 x its FP64-equivalent rate"}
+        elif dom == "flush" and mixed and w["k"] == 32:
+            # the tensor-core flush streams G once (read and write): HBM roofline on 2 N^2 8 bytes
+            achieved = fd["bytes"] / max(1, fd["launches"]) / per_launch_s / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "peak_source": f"{peak_src} copy bandwidth; G (N^2 FP64) read and written once per flush"}
         elif dom == "flush" and mixed:
             # double-float MAC = 12 FP32 instructions: peak FP64-equivalent rate = FP32 FMA issue rate / 12 x 2
             achieved = fd["flops"] / max(1, fd["launches"]) / per_launch_s / 1e12

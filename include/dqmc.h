@@ -113,8 +113,10 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *   "k"          delay rank (4, 8, 16, 32 or 64; default 32);
  *   "n_stab"     slices between UDV refreshes (default 10);
  *   "precision"  0 = plain FP64 (default);
- *                1 = mixed: FP64 data; rank-m flush in double-float
- *                    arithmetic (FP32 pairs, ~2^-47) on the FP32 units, FFT
+ *                1 = mixed: FP64 data; rank-m flush as FP64-accurate
+ *                    digit slices on the tcgen05 tensor cores at k = 32 (see
+ *                    "flush_tc"), else in double-float arithmetic (FP32
+ *                    pairs, ~2^-47) on the FP32 units; FFT
  *                    propagation in FP64 (see "df_prop"); stabilisation
  *                    products as exact digit slices
  *                    on the bf16 tensor cores; Metropolis decisions and
@@ -138,6 +140,11 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                itself; 0 = only what it needs;
  * mixed precision only (1 = double-float, 0 = native FP64 for that step):
  *   "df_flush"   rank-m flush as double-float products (default 1);
+ *   "flush_tc"   with df_flush = 1 and k = 32: the flush as digit slices on
+ *                tcgen05 (dqmc_op_flush_tc), the blocks one after another on
+ *                the context's stream ("pipeline" does not apply) (default 1;
+ *                0 = the double-float flush); a bounded wait of its kernel
+ *                that gives up makes dqmc_sweep return DQMC_ETIMEOUT;
  *   "df_prop"    FFT propagation in double-float arithmetic (default 0: the
  *                propagation is ~4% of a sweep, and its rounding, applied to
  *                the whole G every slice, dominated the double-float drift at
@@ -170,7 +177,7 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                CholeskyQR in mixed precision only. dqmc_green always uses
  *                Householder QR. A non-positive Cholesky pivot makes
  *                dqmc_sweep return DQMC_ENUMERIC.
- * "k", "n_stab", "precision", "chain", "df_flush", "df_prop", "df_metro",
+ * "k", "n_stab", "precision", "chain", "df_flush", "flush_tc", "df_prop", "df_metro",
  * "stab_gemm", "stab_qr" and "gemm_df_sites" are accepted only before the first sweep;
  * later they return DQMC_ESTATE. */
 dqmc_status dqmc_set_option(dqmc_ctx *ctx, const char *key, double value);
@@ -337,6 +344,19 @@ dqmc_status dqmc_op_flush_df(int N, int site0, int kb, double *G, const double *
 dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *Gcol,
                               const float *Grow, const double *alpha, const double *beta,
                               const int *accept_count, void *stream);
+/* The same flush, FP64 G, with the product on the tcgen05 tensor cores:
+ * the N x kb factors A = Gcol alpha^T and B^T = beta (E_S - Grow) in
+ * double-float arithmetic, cut into seven 8-bit digits per entry (row-wise
+ * power-of-two scaling) and multiplied digit pair by digit pair (28 pairs,
+ * exact FP32 accumulation in tensor memory), the levels combined exactly in
+ * integers and subtracted from G in FP64: FP64-accurate like _df. The mixed
+ * precision sweep's flush at delay rank 32. Requires kb <= 32 (else
+ * DQMC_EINVAL); scratch (~0.9 KB per row of G) is allocated and freed on the
+ * stream. A bounded wait inside the kernel that gives up returns
+ * DQMC_ETIMEOUT with G unchanged in the tiles it covers. */
+dqmc_status dqmc_op_flush_tc(int N, int site0, int kb, double *G, const double *Gcol,
+                             const double *Grow, const double *alpha, const double *beta,
+                             const int *accept_count, void *stream);
 
 /* dqmc_op_flush_f64 without any device allocation. The paper has no
  * counterpart: it is a deployment variant of dqmc_op_flush_f64 (above) for

@@ -69,6 +69,7 @@ SIGNATURES = {
     "dqmc_op_flush_f64": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_df": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_f32": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
+    "dqmc_op_flush_tc": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_flush_f64_noalloc": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
     "dqmc_op_measure": (i32, [i32, vp, i32, vp, vp]),
     "dqmc_op_measure_fullq": (i32, [i32, vp, i32, vp, vp, vp]),

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <array>
 #include <atomic>
 #include <cmath>
@@ -220,6 +221,8 @@ struct dqmc_ctx {
   int stab_gemm = 2;  // mixed: stabilisation GEMMs 0 FP64, 1 double-float, 2 tensor-core digit slices
   int stab_qr = 0;    // 0 Householder QR, 1 CholeskyQR2, -1 = CholeskyQR2 in mixed precision only
   int tc_gemm = 1;    // mixed, digit slices: tcgen05 GEMM (else the mma.sync one)
+  int flush_tc = 1;   // mixed, k = 32: rank-m flush as digit slices on tcgen05 (else double-float)
+  void *tcws = nullptr;  // its digit tiles and row exponents
   bool cholqr = false;  // the sweep's stabilisation uses CholeskyQR2 (resolved at allocation)
   unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
   unsigned gemm_df_sites = 0u;        // mixed: of those, the sites that use double-float products
@@ -369,6 +372,12 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
     CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   }
   DQ_CHECK(ctx_alloc(c, &c->Abuf, 2 * (size_t)N * c->k * sizeof(double)));
+  if (c->precision == 1 && c->df_flush && c->flush_tc && c->k == 32) {
+    // digit tiles: rows beyond N are never written and must stay zero
+    const size_t b = flush_tc_workspace_bytes(N);
+    DQ_CHECK(ctx_alloc(c, &c->tcws, b));
+    CK(cudaMemsetAsync(c->tcws, 0, b, c->stream));
+  }
   DQ_CHECK(ctx_alloc_n(c, &c->acc, 4));
   DQ_CHECK(ctx_alloc_n(c, &c->status, 4));
   DQ_CHECK(ctx_alloc_n(c, &c->total_acc, 1));
@@ -537,6 +546,59 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
   ma.c3 = ((uint32_t)c->chain & 0xffffffu) | (kDomainMetropolis << 24);
   ma.slice0 = l - 1;
   int8_t *s = c->field + (size_t)(l - 1) * N;
+  if constexpr (std::is_same<T, double>::value) {
+    if (df && c->tcws && K == 32) {
+      // tensor-core flush. Per block on the context's stream: the digit
+      // tiles (which also form the next block's rows of A), the look-ahead
+      // G'[S', S'], then the flush, which gathers the next block's rows and
+      // columns; the next block's Metropolis runs on the side stream between
+      // the look-ahead and the next digit tiles, beside the flush.
+      ma.s0 = 0;
+      ma.kb = std::min(K, N);
+      ma.ld_g = N;
+      CK(launch_metropolis(ma, Gr[0], false, s, forced, c->coef_a, c->coef_b, c->acc, c->status, c->total_acc,
+                           c->stream, dfm));
+      for (int b = 0; b < nblk; ++b) {
+        const int s0 = b * K, kb = std::min(K, N - s0);
+        const int par = b & 1;
+        double *al = c->coef_a + par * KK, *be = c->coef_b + par * KK;
+        int *acc = c->acc + par;
+        FlushArgs fa;
+        fa.N = N;
+        fa.s0 = s0;
+        fa.kb = kb;
+        fa.ns0 = (b + 1 < nblk) ? s0 + K : 0;
+        fa.nkb = (b + 1 < nblk) ? std::min(K, N - s0 - K) : 0;
+        fa.rows_per_cta = 0;
+        fa.ldc = K;
+        fa.ldb = K;
+        fa.lda = K;
+        float2 *Anext = fa.nkb > 0 ? static_cast<float2 *>(c->Abuf) : nullptr;
+        CK(launch_flush_tc_prep(fa, Gc[par], Gr[par], al, be, acc, c->tcws, Anext, c->stream));
+        if (fa.nkb > 0) {
+          CK(launch_lookahead_g<double>(K, fa, G, c->Abuf, true, Gr[par], be, acc, c->gnext, c->stream));
+          cudaStream_t ms = c->stream;
+          if (c->pipeline) {
+            CK(cudaEventRecord(c->ev_fork, c->stream));
+            CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+            ms = c->side;
+          }
+          MetroArgs mn = ma;
+          mn.s0 = fa.ns0;
+          mn.kb = fa.nkb;
+          mn.ld_g = fa.nkb;
+          CK(launch_metropolis(mn, c->gnext, false, s, forced ? forced + fa.ns0 : nullptr,
+                               c->coef_a + (par ^ 1) * KK, c->coef_b + (par ^ 1) * KK, c->acc + (par ^ 1),
+                               c->status, c->total_acc, ms, dfm));
+          if (c->pipeline) CK(cudaEventRecord(c->ev_join, c->side));
+        }
+        CK(launch_flush_tc_update(fa, G, acc, c->tcws, Gc[par ^ 1], Gr[par ^ 1], c->stream));
+        if (fa.nkb > 0 && c->pipeline) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+      }
+      c->proposed += N;
+      return DQMC_OK;
+    }
+  }
   // block 0: decisions on the context's stream from the gathered rows
   ma.s0 = 0;
   ma.kb = std::min(K, N);
@@ -947,6 +1009,8 @@ dqmc_status read_status(dqmc_ctx *c) {
   c->max_drift = std::max(c->max_drift, dm);
   if (c->precision == 1 && c->stab_gemm == 2 && c->tc_gemm && oz_tc_timed_out(c->stream))
     return poison(c, fail(DQMC_ETIMEOUT, "a bounded wait of the tcgen05 GEMM gave up"));
+  if (c->tcws && flush_tc_timed_out(c->stream))
+    return poison(c, fail(DQMC_ETIMEOUT, "a bounded wait of the tcgen05 flush gave up"));
   if (st[0] != 0) return fail(DQMC_ENUMERIC, "non-positive or non-finite acceptance ratio");
   if (st[1] != 0)
     return fail(DQMC_ENUMERIC, "non-positive pivot in the Cholesky factorisation of the CholeskyQR2 "
@@ -1047,6 +1111,9 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
     c->stab_gemm = (int)v;
   } else if (k == "tc_gemm") {
     c->tc_gemm = v != 0.0;
+  } else if (k == "flush_tc") {
+    if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
+    c->flush_tc = v != 0.0;
   } else if (k == "stab_qr") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     if (v != 0.0 && v != 1.0 && v != -1.0) return fail(DQMC_EINVAL, "stab_qr must be -1 (auto), 0 or 1");

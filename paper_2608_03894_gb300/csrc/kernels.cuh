@@ -79,6 +79,25 @@ cudaError_t launch_lookahead_g(int K, const FlushArgs &a, const T *G, const void
                                const T *Grow, const double *beta, const int *acc, double *gnext,
                                cudaStream_t st);
 
+// The FP64-accurate flush on tcgen05 (flush_tc.cu), delay rank K = 32
+// (a.kb, a.nkb <= 32; row strides ldc = lda = ldb = 32): the A and B factors
+// as digit tiles in ws (flush_tc_workspace_bytes, 256-byte aligned, zeroed
+// once before first use), then G <- G - A B^T with the next block's gather
+// into Gcol_next (N x 32) / Grow_next (a.nkb x N). flush_tc_timed_out:
+// whether a bounded wait of the flush kernel gave up (synchronises st).
+size_t flush_tc_workspace_bytes(int N);
+cudaError_t launch_flush_tc(const FlushArgs &a, double *G, const double *Gcol, const double *Grow,
+                            const double *alpha, const double *beta, const int *acc, void *ws,
+                            double *Gcol_next, double *Grow_next, cudaStream_t st);
+bool flush_tc_timed_out(cudaStream_t st);
+// The two launches of launch_flush_tc: the digit tiles (and, when Anext is
+// not NULL, the next block's rows of A as double-float pairs, Anext[i * 32 +
+// r] for a.ns0 <= i < a.ns0 + a.nkb, for the look-ahead), then the update.
+cudaError_t launch_flush_tc_prep(const FlushArgs &a, const double *Gcol, const double *Grow, const double *alpha,
+                                 const double *beta, const int *acc, void *ws, float2 *Anext, cudaStream_t st);
+cudaError_t launch_flush_tc_update(const FlushArgs &a, double *G, const int *acc, void *ws, double *Gcol_next,
+                                   double *Grow_next, cudaStream_t st);
+
 // ---- measurement (measure.cu)
 struct MeasTables {
   const double *pc, *ps;    // e^{i Q r} for Q = Gamma + dk

@@ -190,6 +190,26 @@ dqmc_status dqmc_op_flush_f32(int N, int site0, int kb, float *G, const float *G
   return op_flush<float>(N, site0, kb, G, Gcol, Grow, alpha, beta, accept_count, false, stream);
 } DQ_API_CATCH
 
+dqmc_status dqmc_op_flush_tc(int N, int site0, int kb, double *G, const double *Gcol,
+                             const double *Grow, const double *alpha, const double *beta,
+                             const int *accept_count, void *stream) try {
+  if (N < 1 || kb < 1 || kb > 32 || site0 < 0 || site0 + kb > N)
+    return fail(DQMC_EINVAL, "need 1 <= kb <= 32 and 0 <= site0, site0 + kb <= N");
+  if (!G || !Gcol || !Grow || !alpha || !beta || !accept_count) return fail(DQMC_EINVAL, "null pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t wb = flush_tc_workspace_bytes(N);
+  void *ws = nullptr;
+  DQ_CUDA(cudaMallocAsync(&ws, wb, st));
+  FlushArgs a{N, site0, kb, 0, 0, 0, kb, kb, kb};
+  cudaError_t e = cudaMemsetAsync(ws, 0, wb, st);
+  if (e == cudaSuccess) e = launch_flush_tc(a, G, Gcol, Grow, alpha, beta, accept_count, ws, nullptr, nullptr, st);
+  const cudaError_t e2 = cudaFreeAsync(ws, st);
+  if (e != cudaSuccess) return cuda_fail(e, "flush_tc");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  if (flush_tc_timed_out(st)) return fail(DQMC_ETIMEOUT, "a bounded wait of the tcgen05 flush gave up");
+  return DQMC_OK;
+} DQ_API_CATCH
+
 dqmc_status dqmc_op_gemm_f64(int mode, int ta, int tb, int M, int N, int K, double alpha,
                              const double *A, int lda, const double *B, int ldb, double beta,
                              double *C, int ldc, void *stream) try {

@@ -16,13 +16,15 @@
 // (weights 2^{7(7-l)}), levels 8..10 into an FP32 accumulator; the FP64
 // result is formed once per output.
 //
-// Tensor path: legacy warp-level mma.sync m16n8k16 bf16 (measured 0.6 PFLOP/s
-// on this part); a tcgen05/TMEM version would be the next step.
+// Tensor paths: warp-level mma.sync m16n8k16 bf16 for every shape, and for
+// products with M, N, K >= 256 a tcgen05 kernel (tensor-memory accumulators,
+// bulk-copy staging) further down.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "kernels.cuh"
 #include "linalg.cuh"
+#include "tc05.cuh"
 
 namespace dq {
 
@@ -357,10 +359,10 @@ __global__ void __launch_bounds__(256)
 // Tensor memory: 512 columns; level l = p + q (2..10) accumulates in columns
 // 48 (l - 2) .. 48 (l - 2) + 47, lane = output row. Every 128 positions of K
 // (eight stages) the sums of levels 2..6 are exact integers below 2^24 (a
-// level has at most 5 digit pairs: 5 * 128 * 127^2 < 2^24); all threads wait
-// for the MMAs, load their row of those levels (tcgen05.ld 32x32b: warps w
-// and w + 4 read lanes 32 (w % 4) .. + 31, columns 0..23 and 24..47) and
-// fold them into an exact int64 accumulator
+// level has at most 5 digit pairs: 5 * 128 * 127^2 < 2^24); the four fold
+// warps wait for the MMAs, load their rows of those levels (tcgen05.ld
+// 32x32b: warp w reads lanes 32 w .. 32 w + 31) and fold them into an exact
+// int64 accumulator
 // (weights 2^{7(6-l)}); the next period's first MMA of each of these levels
 // overwrites (enable-input-d false). Levels 7..10 keep accumulating in FP32
 // over the whole K (their rounding stays below 2^-53 of the level-2 sum) and
@@ -375,86 +377,10 @@ constexpr int TC_A_PLANE = TC_BM * TC_BK * 2, TC_B_PLANE = TC_BN * TC_BK * 2;
 constexpr int TC_DIG = OZ_S * (TC_A_PLANE + TC_B_PLANE);                 // 50688 B per stage
 constexpr int TC_SMEM = TC_NS * TC_DIG + 128;                            // + mbarriers, TMEM address, abort flag
 constexpr int TC_TMEM_COLS = 512;
-constexpr uint32_t TC_IDESC = (1u << 4)                       // D: FP32
-                              | (1u << 7) | (1u << 10)        // A, B: bf16
-                              | ((uint32_t)(TC_BN >> 3) << 17)  // N >> 3
-                              | ((uint32_t)(TC_BM >> 4) << 24); // M >> 4; both operands K-major
-constexpr int TC_WAIT_LIMIT = 1 << 26;  // polls (~0.1-1 s)
+constexpr uint32_t TC_IDESC = tc5::idesc_bf16(TC_BM, TC_BN);
 constexpr int TC_FOLD = 8;  // stages per fold of the exact levels (128 positions)
 
 __device__ int g_oz_tc_timeout = 0;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-// shared-memory matrix descriptor of a K-major tile with 32-byte rows (16
-// bf16 positions) in the 32-byte swizzle: start, leading byte offset 16
-// (unused: one K = 16 step is the whole row), stride byte offset 256 (8-row
-// groups), version 1, layout type 6
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(16 >> 4) << 16) |
-         ((uint64_t)(256 >> 4) << 32) | (1ull << 46) | (6ull << 61);
-}
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, int bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes));
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait_n() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-// Spin on the phase with the non-blocking test (try_wait may suspend the
-// thread for a system-dependent time, which here would add its wake-up
-// latency to every stage); bounded.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred P;\n mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(acc));
-}
-__device__ __forceinline__ void tc_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
-               : "memory");
-}
-// 8 columns of this warp's 32 lanes into v[0..7]; the caller waits
-__device__ __forceinline__ void tc_ld8_nowait(uint32_t taddr, float *v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-// 16 columns of this warp's 32 lanes into v[0..15]; the caller waits (tcgen05.wait::ld)
-__device__ __forceinline__ void tc_ld16_nowait(uint32_t taddr, float *v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Stage `st` (positions k0 .. k0 + 15) of the digit planes into slot b by one
 // thread: per plane, the 128 rows of the A tile and the 48 of the B tile are
@@ -472,11 +398,11 @@ __device__ __forceinline__ void tc_stage_bulk(uint32_t sdig, int b, uint32_t mba
   const int ra = min(TC_BM, M - m0), rb = min(TC_BN, N - n0);
   const uint32_t stage = sdig + b * TC_DIG;
   const size_t kb = (size_t)(k0 >> 4);
-  mbar_expect_tx(mbar, tc_stage_bytes(M, N, m0, n0));
+  tc5::mbar_expect_tx(mbar, tc_stage_bytes(M, N, m0, n0));
 #pragma unroll 1
   for (int p = 0; p < OZ_S; ++p) {
-    bulk_copy(stage + p * TC_A_PLANE, Ad + p * aplane + (kb * M + m0) * 16, (uint32_t)ra * 32, mbar);
-    bulk_copy(stage + OZ_S * TC_A_PLANE + p * TC_B_PLANE, Bd + p * bplane + (kb * N + n0) * 16, (uint32_t)rb * 32,
+    tc5::bulk_copy(stage + p * TC_A_PLANE, Ad + p * aplane + (kb * M + m0) * 16, (uint32_t)ra * 32, mbar);
+    tc5::bulk_copy(stage + OZ_S * TC_A_PLANE + p * TC_B_PLANE, Bd + p * bplane + (kb * N + n0) * 16, (uint32_t)rb * 32,
               mbar);
   }
 }
@@ -493,25 +419,6 @@ __device__ __forceinline__ void tc_stage_bulk(uint32_t sdig, int b, uint32_t mba
 constexpr int TC_THREADS = 192;
 constexpr int TC_COPY0 = 160;  // the copy thread (warp 5, lane 0)
 
-// Bounded phase wait that also gives up when another role has aborted.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t addr, uint32_t parity, volatile int *abort) {
-  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred P;\n mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if ((it & 1023) == 1023 && *abort) return false;
-  }
-  *abort = 1;
-  return false;
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(addr) : "memory");
-}
-
 __global__ void __launch_bounds__(TC_THREADS, 1)
     oz_gemm_tc_kernel(int M, int N, int Kp, const unsigned short *__restrict__ Ad,
                       const unsigned short *__restrict__ Bd, const int *__restrict__ ea,
@@ -522,10 +429,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
   const size_t aplane = (size_t)M * Kp, bplane = (size_t)N * Kp;
-  const uint32_t sdig = smem_u32(tsm);
+  const uint32_t sdig = tc5::smem_u32(tsm);
   // mbarriers: full[4], empty[4], acc, freed; then the TMEM address and the abort flag
   unsigned char *ctl = tsm + TC_NS * TC_DIG;
-  const uint32_t mb = smem_u32(ctl);
+  const uint32_t mb = tc5::smem_u32(ctl);
   const uint32_t mb_full = mb, mb_empty = mb + 8 * TC_NS, mb_acc = mb + 16 * TC_NS, mb_freed = mb_acc + 8;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(ctl + 16 * TC_NS + 16);
   volatile int *abort = reinterpret_cast<volatile int *>(ctl + 16 * TC_NS + 20);
@@ -541,7 +448,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     *abort = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc5::smem_u32(tslot)),
                  "r"(TC_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
@@ -559,20 +466,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---- copier: stage st into slot st % 4 once the MMAs of stage st - 4 are done
     for (int st = 0; st < nst; ++st) {
       const int b = st % TC_NS;
-      if (st >= TC_NS && !mbar_wait_or_abort(mb_empty + 8 * b, ((st / TC_NS) - 1) & 1, abort)) break;
+      if (st >= TC_NS && !tc5::mbar_wait_or_abort(mb_empty + 8 * b, ((st / TC_NS) - 1) & 1, abort)) break;
       tc_stage_bulk(sdig, b, mb_full + 8 * b, Ad, Bd, M, N, m0, n0, (sbeg + st) * TC_BK, aplane, bplane);
     }
   } else if (tid == 128) {
     // ---- MMA issuer
     for (int st = 0; st < nst; ++st) {
       const int b = st % TC_NS;
-      if (!mbar_wait_or_abort(mb_full + 8 * b, (st / TC_NS) & 1, abort)) break;
+      if (!tc5::mbar_wait_or_abort(mb_full + 8 * b, (st / TC_NS) & 1, abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint64_t ad0 = tc_desc(sdig + b * TC_DIG), bd0 = tc_desc(sdig + b * TC_DIG + OZ_S * TC_A_PLANE);
+      const uint64_t ad0 = tc5::desc(sdig + b * TC_DIG), bd0 = tc5::desc(sdig + b * TC_DIG + OZ_S * TC_A_PLANE);
       // a new fold period overwrites the exact levels: the previous fold must have read them
       const bool restart = (st % TC_FOLD) == 0;
       if (st > 0 && restart) {
-        if (!mbar_wait_or_abort(mb_freed, ((st / TC_FOLD) - 1) & 1, abort)) break;
+        if (!tc5::mbar_wait_or_abort(mb_freed, ((st / TC_FOLD) - 1) & 1, abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       }
       // exact levels 2..6 restart every TC_FOLD stages, 7..10 only at the first
@@ -581,11 +488,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll 1
         for (int q = 0; p + q <= OZ_S - 1; ++q) {
           const uint32_t accf = (restart && p == 0 && (q <= 4 || st == 0)) ? 0u : 1u;
-          tc_mma(tbase + (uint32_t)((p + q) * TC_BN), ad0 + (uint64_t)((p * TC_A_PLANE) >> 4),
-                 bd0 + (uint64_t)((q * TC_B_PLANE) >> 4), accf);
+          tc5::mma(tbase + (uint32_t)((p + q) * TC_BN), ad0 + (uint64_t)((p * TC_A_PLANE) >> 4),
+                 bd0 + (uint64_t)((q * TC_B_PLANE) >> 4), TC_IDESC, accf);
         }
-      tc_commit(mb_empty + 8 * b);
-      if ((st % TC_FOLD) == TC_FOLD - 1 || st == nst - 1) tc_commit(mb_acc);
+      tc5::commit(mb_empty + 8 * b);
+      if ((st % TC_FOLD) == TC_FOLD - 1 || st == nst - 1) tc5::commit(mb_acc);
     }
   }
 
@@ -600,7 +507,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int f = 0; f < nfold && ok; ++f) {
       // lane 0 polls and the warp follows its verdict, so the aligned
       // tensor-memory loads stay warp-uniform
-      int okw = lane == 0 ? (int)mbar_wait_or_abort(mb_acc, f & 1, abort) : 0;
+      int okw = lane == 0 ? (int)tc5::mbar_sleep_wait(mb_acc, f & 1, abort) : 0;
       ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -610,7 +517,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int ch = 0; ch < TC_BN / 16; ++ch) {
           float v[16];
-          tc_ld16_nowait(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
+          tc5::ld16(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
           for (int c = 0; c < 16; ++c) I[ch * 16 + c] += ((long long)__float2int_rn(v[c])) << (7 * (6 - l));
@@ -618,7 +525,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(mb_freed);
+      if (lane == 0) tc5::mbar_arrive(mb_freed);
     }
     // levels 7..10 (weights 2^{-7(l-6)}) are read once, 16 columns at a time
     // (the last fold waited for every MMA), and the outputs formed:
@@ -635,7 +542,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int idx = 5; idx < OZ_S; ++idx) {
           const float w = __int_as_float((127 - 7 * (idx - 4)) << 23);
           float v[16];
-          tc_ld16_nowait(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
+          tc5::ld16(trow + (uint32_t)(idx * TC_BN + ch * 16), v);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
           for (int c = 0; c < 16; ++c) F[c] = fmaf(v[c], w, F[c]);
@@ -670,15 +577,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   }
-  cp_async_wait_n<0>();
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   if (__syncthreads_or(*abort)) {
     // give the MMAs already issued a bounded time to finish before the tensor memory goes
     if (tid == 128) {
       volatile int *never = abort + 1;  // a flag nothing sets: the drain runs to its own limit
       *never = 0;
-      tc_commit(mb_acc);
-      mbar_wait_or_abort(mb_acc, nfold & 1, never);
+      tc5::commit(mb_acc);
+      tc5::mbar_wait_or_abort(mb_acc, nfold & 1, never);
       atomicExch(&g_oz_tc_timeout, 1);
     }
     __syncthreads();

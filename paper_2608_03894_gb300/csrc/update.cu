@@ -10,12 +10,15 @@
 // rank-m update, written as G' = G - A B^T with A = G[:,S] alpha^T and
 // B^T = beta (E_S - G[S,:]), where alpha^T beta = Gamma on (P, P).
 //
-// Kernels: the Metropolis block (one CTA, FP64), the A factor (and, for the
-// double-float flush, the B factor), the look-ahead G'[S',S'] of the next
-// block from the pre-flush G (so that the next block's decisions can run
-// while this block's flush streams G), and the flush itself -- FP64 / FP32 by
-// column stripes, or double-float by 64 x 64 tiles -- whose epilogue gathers
-// G[:,S'] and G[S',:] of the next block.
+// Kernels: the Metropolis block (one CTA: 16 warps with the block in
+// registers for k <= 32, else a shared-memory form; FP64 or double-float),
+// the A factor (and, for the double-float flush, the B factor), the
+// look-ahead G'[S',S'] of the next block from the pre-flush G (so that the
+// next block's decisions can run while this block's flush streams G), and
+// the flush itself -- FP64 / FP32 by column stripes, or double-float by
+// 64 x 64 tiles -- whose epilogue gathers G[:,S'] and G[S',:] of the next
+// block. The tensor-core flush of the mixed precision sweep is in
+// flush_tc.cu.
 #include <algorithm>
 #include <type_traits>
 
@@ -92,6 +95,7 @@ template <> struct MetroMath<double> {
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ bool positive(double a) { return a > 0.0; }
   static __device__ __forceinline__ bool finite(double a) { return isfinite(a); }
+  static __device__ __forceinline__ float hi(double a) { return (float)a; }
 };
 template <> struct MetroMath<df64> {
   static __device__ __forceinline__ df64 from(double x) { return df_from(x); }
@@ -106,6 +110,7 @@ template <> struct MetroMath<df64> {
   }
   static __device__ __forceinline__ bool positive(df64 a) { return a.hi > 0.f || (a.hi == 0.f && a.lo > 0.f); }
   static __device__ __forceinline__ bool finite(df64 a) { return isfinite(a.hi); }
+  static __device__ __forceinline__ float hi(df64 a) { return a.hi; }
 };
 
 // One CTA of 4 x NC threads (NC = 32 or 64 block columns): thread (w, v) owns
@@ -245,6 +250,197 @@ __global__ void __launch_bounds__(4 * NC)
   }
 }
 
+// The same block for kb <= 32 on 16 warps, the block in registers. Warp w
+// holds rows w and w + 16 of g~ (lane v = column v), so that the trailing
+// update of an accepted flip costs every warp two multiply-adds. Site j: the
+// warp holding row j takes the decision (an FP32 screen decides unless the
+// uniform lies within 1e-5 of the ratio, the full arithmetic otherwise, so
+// the decisions are those of metropolis_block_kernel), publishes the decision,
+// its coefficient delta / r and row j in shared memory, and one CTA barrier
+// hands them to the other warps, which update their rows i > j with one
+// broadcast of column j within the warp. Gauss-Jordan on Delta^{-1} + I -
+// G[P,P] then runs on the same layout with one barrier per pivot; the pivot of
+// step p is the Schur complement r_p / delta_p of the decision chain, so its
+// reciprocal is the flip's coefficient delta_p / r_p. All global loads are
+// issued before the conversions that use them.
+template <typename T>
+__device__ __forceinline__ T shfl_t(T x, int src);
+template <>
+__device__ __forceinline__ double shfl_t<double>(double x, int src) {
+  return __shfl_sync(0xffffffffu, x, src);
+}
+template <>
+__device__ __forceinline__ df64 shfl_t<df64>(df64 x, int src) {
+  return df64(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
+}
+
+constexpr int kMetroCta = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kMetroCta)
+    metropolis_cta_kernel(MetroArgs a, const void *__restrict__ g_, int g_is_f32, int8_t *s,
+                          const uint8_t *__restrict__ forced, double *__restrict__ alpha_out,
+                          double *__restrict__ beta_out, int *accept_count, int *status,
+                          unsigned long long *total) {
+  using MM = MetroMath<T>;
+  __shared__ T s_row[2][32];
+  __shared__ T s_c[2];
+  __shared__ int s_dec[2];
+  __shared__ int s_P[32];
+  __shared__ T s_dinv[32], s_cinv[32];
+  __shared__ double s_u[32];
+  __shared__ int s_spin[32], s_forced[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kb = a.kb;
+  auto gin = [&](int r, int c) -> double {
+    const size_t off = (size_t)r * a.ld_g + c;
+    return g_is_f32 ? (double)static_cast<const float *>(g_)[off] : static_cast<const double *>(g_)[off];
+  };
+  const T one = MM::from(1.0), zero = MM::from(0.0);
+  const T dpos = MM::from(a.em2l - 1.0), dneg = MM::from(a.e2l - 1.0);  // delta for s = +1 / -1
+  const T epos = MM::from(a.e2l), eneg = MM::from(a.em2l);
+  const float dposf = (float)(a.em2l - 1.0), dnegf = (float)(a.e2l - 1.0);
+  const float eposf = (float)a.e2l, enegf = (float)a.em2l;
+
+  T x[2];
+  {
+    double gr[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = warp + 16 * q;
+      gr[q] = (i < kb && lane < kb) ? gin(i, lane) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) x[q] = MM::from(gr[q]);
+  }
+  if (tid < kb) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(a.s0 + tid), (uint32_t)a.slice0, a.c2, a.c3), a.k0, a.k1);
+    s_u[tid] = uniform53(r.x, r.y);
+    s_spin[tid] = (int)s[a.s0 + tid];
+    s_forced[tid] = forced ? (int)forced[tid] : 0;
+  }
+  __syncthreads();
+
+  int m = 0, failed = 0;
+#pragma unroll 1
+  for (int j = 0; j < kb; ++j) {
+    const int buf = j & 1;
+    if (warp == (j & 15)) {
+      const T rowj = (j >> 4) ? x[1] : x[0];  // g~[j][lane]
+      const T gjj = shfl_t(rowj, j);
+      const int sj = s_spin[j];
+      const double uj = s_u[j];
+      // delta = e^{-2 lambda s} - 1, r = 1 + delta (1 - g~_jj), R = e^{2 lambda s} r^2
+      const T delta = sj > 0 ? dpos : dneg;
+      int dec = -2;
+      if (!forced) {
+        const float rf = fmaf(sj > 0 ? dposf : dnegf, 1.f - MM::hi(gjj), 1.f);
+        const float Rf = (sj > 0 ? eposf : enegf) * rf * rf;
+        const float uf = (float)uj;
+        if (Rf > 0.f && Rf < 1e30f) {
+          if (uf < Rf * (1.f - 1e-5f)) dec = 1;
+          else if (uf > Rf * (1.f + 1e-5f)) dec = 0;
+        }
+      }
+      const T r = MM::mad(delta, one - gjj, one);
+      if (dec == -2) {
+        const T R = (sj > 0 ? epos : eneg) * r * r;
+        if (!MM::positive(R) || !MM::finite(R))
+          dec = -1;
+        else if (forced)
+          dec = s_forced[j] ? 1 : 0;
+        else
+          dec = MM::positive(R - MM::from(uj)) ? 1 : 0;  // accept iff u < R
+      }
+      s_row[buf][lane] = rowj;
+      if (lane == 0) {
+        s_dec[buf] = dec;
+        if (dec > 0) {
+          const T cj = MM::div(delta, r);
+          s_c[buf] = cj;
+          s_P[m] = j;
+          s_dinv[m] = MM::div(one, delta);
+          s_cinv[m] = cj;
+          s_spin[j] = -sj;
+        }
+      }
+    }
+    __syncthreads();
+    const int dec = s_dec[buf];
+    if (dec < 0) {
+      failed = 1;
+      break;
+    }
+    if (dec == 0) continue;
+    // trailing update g~[i][v] += c g~[j][v] g~[i][j] for the rows i > j of
+    // this warp (columns v <= j are done with and take harmless values)
+    const T cg = s_c[buf] * s_row[buf][lane];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = warp + 16 * q;
+      const T xi = shfl_t(x[q], j);
+      if (i > j) x[q] = MM::mad(cg, xi, x[q]);
+    }
+    ++m;
+  }
+  if (tid < kb) s[a.s0 + tid] = (int8_t)s_spin[tid];
+
+  // Gamma = (Delta^{-1} + I - G[P,P])^{-1} by in-place Gauss-Jordan, P in order
+  {
+    double g0[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = warp + 16 * q;
+      g0[q] = (i < m && lane < m) ? gin(s_P[i], s_P[lane]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = warp + 16 * q;
+      x[q] = (i < m && lane < m) ? (i == lane ? one + s_dinv[i] : zero) - MM::from(g0[q]) : zero;
+    }
+  }
+#pragma unroll 1
+  for (int p = 0; p < m; ++p) {
+    const int buf = p & 1;
+    const T pinv = s_cinv[p];
+    if (warp == (p & 15)) {
+      const T xp = (p >> 4) ? x[1] : x[0];
+      const T nr = (lane == p) ? pinv : xp * pinv;
+      if (p >> 4)
+        x[1] = nr;
+      else
+        x[0] = nr;
+      s_row[buf][lane] = nr;
+    }
+    __syncthreads();
+    const T rp = s_row[buf][lane];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = warp + 16 * q;
+      const T f = shfl_t(x[q], p);
+      if (i < m && i != p) x[q] = (lane == p) ? -(f * pinv) : MM::mad(-f, rp, x[q]);
+    }
+  }
+
+  // alpha[r][P_q] = Gamma[q][r], beta[r][P_r] = 1 (row stride K); the rest zero
+  for (int e = tid; e < a.K * a.K; e += kMetroCta) {
+    alpha_out[e] = 0.0;
+    beta_out[e] = 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int i = warp + 16 * q;
+    if (i < m && lane < m) alpha_out[lane * a.K + s_P[i]] = MM::to(x[q]);
+  }
+  if (tid < m) beta_out[tid * a.K + s_P[tid]] = 1.0;
+  if (tid == 0) {
+    *accept_count = m;
+    if (failed) *status = 1;
+    if (total) atomicAdd(total, (unsigned long long)m);
+  }
+}
+
 template <int NC, typename T>
 static cudaError_t launch_metro_t(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
                                   const uint8_t *forced, double *alpha, double *beta, int *accept_count,
@@ -265,12 +461,34 @@ static cudaError_t launch_metro_t(const MetroArgs &a, const void *g, bool g_f32,
   return cudaGetLastError();
 }
 
+// the 16-warp form of the block (kb <= 32)
+template <typename T>
+static cudaError_t launch_metro_cta(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
+                                    const uint8_t *forced, double *alpha, double *beta, int *accept_count,
+                                    int *status, unsigned long long *total, cudaStream_t st, int reserve_smem) {
+  const size_t smem = reserve_smem > 0 ? std::min<size_t>((size_t)reserve_smem, 224 * 1024) : 0;
+  const void *fn = (const void *)metropolis_cta_kernel<T>;
+  if (smem > 0) {
+    cudaError_t e = ensure_smem_attr(fn, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  DQ_KSCOPE(KF_METRO, st);
+  metropolis_cta_kernel<T><<<1, kMetroCta, smem, st>>>(a, g, g_f32 ? 1 : 0, s, forced, alpha, beta, accept_count,
+                                                      status, total);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_metropolis(const MetroArgs &a, const void *g, bool g_f32, int8_t *s,
                               const uint8_t *forced, double *alpha, double *beta, int *accept_count,
                               int *status, unsigned long long *total, cudaStream_t st, bool df,
                               int reserve_smem) {
   if (a.kb < 1 || a.kb > 64 || a.kb > a.K) return cudaErrorInvalidValue;
   const bool wide = a.kb > 32;
+  if (!wide)
+    return df ? launch_metro_cta<df64>(a, g, g_f32, s, forced, alpha, beta, accept_count, status, total, st,
+                                       reserve_smem)
+              : launch_metro_cta<double>(a, g, g_f32, s, forced, alpha, beta, accept_count, status, total, st,
+                                         reserve_smem);
   if (df)
     return wide ? launch_metro_t<64, df64>(a, g, g_f32, s, forced, alpha, beta, accept_count, status, total, st, reserve_smem)
                 : launch_metro_t<32, df64>(a, g, g_f32, s, forced, alpha, beta, accept_count, status, total, st, reserve_smem);

@@ -75,7 +75,8 @@ def metropolis_block(N, site0, kb, g, s, lam, seed, chain, sweep_pass, slice1, f
 
 def flush(N, site0, kb, G, Gcol, Grow, alpha, beta, count, mode=None):
     """G <- G - (Gcol alpha^T)(beta (E_S - Grow)) in place. mode: "f64" (default for
-    float64 G), "df" (FP64 G, double-float product) or "f32" (float32 G)."""
+    float64 G), "df" (FP64 G, double-float product), "tc" (FP64 G, digit-slice
+    product on the tcgen05 tensor cores, kb <= 32) or "f32" (float32 G)."""
     import torch
     lib = _lib.load()
     dt = G.dtype
@@ -85,7 +86,8 @@ def flush(N, site0, kb, G, Gcol, Grow, alpha, beta, count, mode=None):
     _need(beta, torch.float64, "beta")
     _need(count, torch.int32, "count")
     mode = mode or ("f64" if dt == torch.float64 else "f32")
-    fn = {"f64": lib.dqmc_op_flush_f64, "df": lib.dqmc_op_flush_df, "f32": lib.dqmc_op_flush_f32}[mode]
+    fn = {"f64": lib.dqmc_op_flush_f64, "df": lib.dqmc_op_flush_df, "tc": lib.dqmc_op_flush_tc,
+          "f32": lib.dqmc_op_flush_f32}[mode]
     check(fn(int(N), int(site0), int(kb), _ptr(G), _ptr(Gcol), _ptr(Grow), _ptr(alpha), _ptr(beta),
              _ptr(count), _stream(torch)))
     return G

@@ -80,6 +80,7 @@ def test_create_and_destroy_without_gpu_work(lib):
     assert lib.dqmc_set_option(h, b"stab_qr", 2.0) == 1
     assert lib.dqmc_set_option(h, b"tc_gemm", 0.0) == 0
     assert lib.dqmc_set_option(h, b"df_metro", 0.0) == 0
+    assert lib.dqmc_set_option(h, b"flush_tc", 0.0) == 0
     assert lib.dqmc_set_option(h, b"metro_reserve", 224 * 1024 + 1.0) == 1
     lib.dqmc_destroy(h)
 
@@ -119,6 +120,8 @@ def test_operator_argument_validation(lib):
     assert lib.dqmc_op_flush_f64(48, 40, 16, p, p, p, p, p, p, None) == 1      # site0 + kb > N
     assert lib.dqmc_op_flush_df(48, 0, 65, p, p, p, p, p, p, None) == 1        # kb > 64
     assert lib.dqmc_op_flush_f32(48, 0, 8, p, p, p, None, p, p, None) == 1     # null alpha
+    assert lib.dqmc_op_flush_tc(48, 0, 33, p, p, p, p, p, p, None) == 1        # kb > 32
+    assert lib.dqmc_op_flush_tc(48, 40, 16, p, p, p, p, p, p, None) == 1       # site0 + kb > N
     assert lib.dqmc_op_metropolis_block(48, 0, 65, p, 65, p, 0.5, 1, 0, 0, 1,
                                         None, p, p, p, p, None) == 1
     assert lib.dqmc_op_metropolis_block(48, 0, 8, p, 4, p, 0.5, 1, 0, 0, 1,

@@ -118,7 +118,8 @@ def _oracle_slice_update(L, beta, U, G0, field, l, pas, seed, sweep):
 
 @pytest.mark.parametrize("L,k,mode", [(2, 4, "f64"), (4, 8, "f64"), (4, 32, "f64"), (6, 64, "f64"),
                                       (6, 16, "f64"), (6, 7, "f64"), (4, 32, "df"), (6, 64, "df"),
-                                      (6, 12, "df")])
+                                      (6, 12, "df"), (4, 32, "tc"), (6, 32, "tc"), (6, 12, "tc"),
+                                      (2, 5, "tc")])
 def test_delayed_update_slice_matches_one_at_a_time(pkg, L, k, mode):
     """A whole slice of proposals by blocks of k (Metropolis block + rank-k
     flush) reproduces the oracle's one-at-a-time Sherman-Morrison sweep: same
@@ -138,11 +139,52 @@ def test_delayed_update_slice_matches_one_at_a_time(pkg, L, k, mode):
         Grow = G[s0:s0 + kb, :].contiguous()
         g = G[s0:s0 + kb, s0:s0 + kb].contiguous()
         al, be, cnt, st = pkg.ops.metropolis_block(N, s0, kb, g, s, m.lam, seed, 0, 2 * sweep + pas, l,
-                                                   df=(mode == "df"))
+                                                   df=(mode in ("df", "tc")))
         assert st == 0
         pkg.ops.flush(N, s0, kb, G, Gcol, Grow, al, be, cnt, mode=mode)
     assert np.array_equal(s.cpu().numpy(), fref[l - 1])
     assert np.max(np.abs(G.cpu().numpy() - Gref)) < (1e-12 if mode == "f64" else 1e-11)
+
+
+@pytest.mark.parametrize("L,kb,site0", [(12, 32, 0), (12, 21, 100), (12, 32, 400), (24, 32, 864),
+                                         (24, 9, 1719), (6, 32, 64), (36, 32, 3856)])
+def test_tensor_core_flush_equals_the_fp64_flush(pkg, L, kb, site0):
+    """One block's flush from the same Metropolis output (double-float block
+    on a G-like matrix): the tcgen05 digit-slice flush against the FP64 flush,
+    all N^2 entries, at N not a multiple of the 128-column tile and ragged
+    blocks. The digit slices keep ~2^-55 of each row scale; the factors are
+    formed in double-float (~2^-47), so 1e-13 absolute on |G| ~ 1."""
+    N = 3 * L * L
+    G0 = dev(random_green_like(N, L + kb))
+    s = dev(random_field(1, N, seed=kb)[0], torch.int8)
+    g = G0[site0:site0 + kb, site0:site0 + kb].contiguous()
+    al, be, cnt, st = pkg.ops.metropolis_block(N, site0, kb, g, s, 0.7, 11, 0, 1, 1, df=True)
+    assert st == 0 and int(cnt.item()) > 0
+    Gcol = G0[:, site0:site0 + kb].contiguous()
+    Grow = G0[site0:site0 + kb, :].contiguous()
+    Gt, Gf = G0.clone(), G0.clone()
+    pkg.ops.flush(N, site0, kb, Gt, Gcol, Grow, al, be, cnt, mode="tc")
+    pkg.ops.flush(N, site0, kb, Gf, Gcol, Grow, al, be, cnt, mode="f64")
+    upd = (Gf - G0).abs().max().item()
+    assert upd > 1e-3  # the block changed G
+    assert (Gt - Gf).abs().max().item() < 1e-13
+
+
+def test_tensor_core_flush_sweeps_follow_the_double_float_flush(pkg):
+    """Mixed precision at L = 12, k = 32: three sweeps with the tcgen05 flush
+    and with the double-float flush give the same field and running G within
+    the double-float rounding."""
+    par = dict(L=12, beta=4.0, dtau=0.1, U=-4.0, mu=-1.0)
+    out = []
+    for tc in (1, 0):
+        with pkg.DQMC(**par, seed=4, k=32, n_stab=8, precision="mixed") as d:
+            d.set_option("flush_tc", tc)
+            d.sweep(3)
+            G, _ = d.running_green()
+            out.append((d.field, G, d.stats()["max_drift"]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.max(np.abs(out[0][1] - out[1][1])) < 1e-9
+    assert out[0][2] < 1e-7
 
 
 def test_forced_flips_and_fp32_flush(pkg):
@@ -571,8 +613,8 @@ def test_set_field_to_the_current_state_keeps_g(pkg):
 def test_single_stream_mode_is_bit_identical(pkg, prec):
     """pipeline = 0 (the next block's Metropolis on the context's own stream,
     before the flush) takes the same decisions as the two-stream pipeline and
-    gives the same G (up to the summation order of split-K GEMM partials,
-    which FP64 atomic adds do not fix)."""
+    gives the same G bit for bit (every reduction has a fixed order). In
+    mixed precision at k = 32 this is the tensor-core flush path."""
     par = dict(L=12, beta=2.0, dtau=0.1, U=-4.0, mu=-1.0)
     out = {}
     for pl in (1, 0):
@@ -581,4 +623,4 @@ def test_single_stream_mode_is_bit_identical(pkg, prec):
             d.sweep(2)
             out[pl] = (d.field, d.running_green()[0])
     assert np.array_equal(out[0][0], out[1][0])
-    assert np.max(np.abs(out[0][1] - out[1][1])) < 1e-10
+    assert np.array_equal(out[0][1], out[1][1])
