@@ -18,7 +18,7 @@ WORKLOADS = {
                      precision="fp64", sweeps=1000),
     "L24_mixed": dict(L=24, beta=24.0, dtau=0.1, U=-4.0, mu=-1.0, seed=1, k=32, n_stab=8,
                       precision="mixed"),
-    "L36_mixed": dict(L=36, beta=36.0, dtau=0.1, U=-4.0, mu=-1.0, seed=1, k=64, n_stab=8,
+    "L36_mixed": dict(L=36, beta=36.0, dtau=0.1, U=-4.0, mu=-1.0, seed=1, k=32, n_stab=8,
                       precision="mixed"),
 }
 

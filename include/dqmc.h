@@ -152,6 +152,11 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *   "df_metro"   Metropolis decisions, the tracked k x k block and the
  *                Woodbury coefficients in double-float arithmetic (default 1;
  *                0 = FP64, whose serial chain is ~8x slower on this part);
+ *   "df_panel"   Householder panel column loop (dot products and row
+ *                updates) in double-float arithmetic on columns scaled by
+ *                powers of two, reflector scalars in FP64 (default 0: the
+ *                panel is bound by barrier latency, not by the FP64 pipe, and
+ *                this gains ~2% of an L = 24 sweep for ~2x the drift);
  *   "stab_gemm"  stabilisation GEMMs: 0 = FP64, 1 = double-float, 2 = exact
  *                7-bit digit slices on the bf16 tensor cores (default 2);
  *   "tc_gemm"    with stab_gemm = 2: 1 (default) = the digit-slice products

@@ -222,6 +222,7 @@ struct dqmc_ctx {
   int stab_qr = 0;    // 0 Householder QR, 1 CholeskyQR2, -1 = CholeskyQR2 in mixed precision only
   int tc_gemm = 1;    // mixed, digit slices: tcgen05 GEMM (else the mma.sync one)
   int flush_tc = 1;   // mixed, k = 32: rank-m flush as digit slices on tcgen05 (else double-float)
+  int df_panel = 0;   // mixed: Householder panel column loop in double-float arithmetic
   void *tcws = nullptr;  // its digit tiles and row exponents
   bool cholqr = false;  // the sweep's stabilisation uses CholeskyQR2 (resolved at allocation)
   unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
@@ -792,6 +793,7 @@ struct GemmModeScope {
   explicit GemmModeScope(dqmc_ctx *c) {
     set_splitk_workspace(c->skws, splitk_ws_doubles());
     if (c->precision != 1) return;
+    set_qr_panel_df(c->df_panel != 0);
     if (c->stab_gemm == 1 && c->dfws) {
       set_df_workspace(c->dfws, c->dfws_elems);
       set_gemm_df(true);
@@ -809,6 +811,7 @@ struct GemmModeScope {
   }
   ~GemmModeScope() {
     set_splitk_workspace(nullptr, 0);
+    set_qr_panel_df(false);
     set_gemm_df(false);
     set_gemm_oz(false);
     set_gemm_oz_tc(false);
@@ -1111,6 +1114,8 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
     c->stab_gemm = (int)v;
   } else if (k == "tc_gemm") {
     c->tc_gemm = v != 0.0;
+  } else if (k == "df_panel") {
+    c->df_panel = v != 0.0;
   } else if (k == "flush_tc") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     c->flush_tc = v != 0.0;

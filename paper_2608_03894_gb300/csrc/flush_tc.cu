@@ -101,32 +101,72 @@ __global__ void __launch_bounds__(256)
                          unsigned short *__restrict__ Vd, int *__restrict__ eU, int *__restrict__ eV,
                          int nblk_a, float2 *__restrict__ Anext) {
   __shared__ df64 sc[FT_K][FT_K + 1];  // sc[u][r] = coefficient [r][u]
+  __shared__ int s_sel[FT_K];          // B rows: the column of row r's single 1 (-1: none)
+  __shared__ int s_nz[FT_K], s_nnz, s_general;  // A rows: the columns with a nonzero coefficient
   const int N = a.N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m = accept_count ? *accept_count : a.kb;
   const bool isa = (int)blockIdx.x < nblk_a;
+  const int row = (isa ? (int)blockIdx.x : (int)blockIdx.x - nblk_a) * 8 + warp;
+  // this warp's row inputs, read before the coefficients are staged: lane u
+  // holds G[row, s0 + u] (A rows) or G[s0 + u, row] (B rows)
+  double gin = 0.0;
+  if (row < N && lane < a.kb) gin = isa ? Gcol[(size_t)row * a.ldc + lane] : Grow[(size_t)lane * N + row];
   {
     const double *coef = isa ? alpha : beta;
     const int ld = isa ? a.lda : a.ldb;
+    if (threadIdx.x == 0) {
+      s_nnz = 0;
+      s_general = 0;
+    }
     for (int e = threadIdx.x; e < FT_K * FT_K; e += 256) {
       const int r = e / FT_K, u = e % FT_K;
       sc[u][r] = (r < m && u < a.kb) ? df_from(coef[r * ld + u]) : df64(0.f, 0.f);
     }
+    __syncthreads();
+    if (warp == 0) {
+      // column u of the coefficients holds a nonzero (A), or row r = lane is a
+      // selector: one entry equal to 1, the rest 0 (B)
+      bool nz = false;
+      int sel = -1, ones = 0, other = 0;
+      for (int t = 0; t < FT_K; ++t) {
+        const df64 cu = sc[lane][t], cr = sc[t][lane];  // coefficient [t][lane], coefficient [lane][t]
+        nz = nz || cu.hi != 0.f;
+        if (cr.hi == 1.f && cr.lo == 0.f) {
+          ++ones;
+          sel = t;
+        } else if (cr.hi != 0.f) {
+          ++other;
+        }
+      }
+      if (isa) {
+        const unsigned msk = __ballot_sync(0xffffffffu, nz);
+        if (nz) s_nz[__popc(msk & ((1u << lane) - 1u))] = lane;
+        if (lane == 0) s_nnz = __popc(msk);
+      } else {
+        s_sel[lane] = (lane < m) ? sel : -1;
+        if (__any_sync(0xffffffffu, lane < m && (ones != 1 || other != 0))) s_general = 1;
+      }
+    }
   }
   __syncthreads();
-  const int row = (isa ? (int)blockIdx.x : (int)blockIdx.x - nblk_a) * 8 + warp;
   if (row >= N) return;
   const int r = lane;
+  const df64 gu = df_from(gin);
   df64 x(0.f, 0.f);
   if (isa) {
-    const df64 gu = lane < a.kb ? df_from(Gcol[(size_t)row * a.ldc + lane]) : df64(0.f, 0.f);
-    for (int u = 0; u < a.kb; ++u) {
+    for (int k = 0; k < s_nnz; ++k) {
+      const int u = s_nz[k];
       const df64 gv(__shfl_sync(0xffffffffu, gu.hi, u), __shfl_sync(0xffffffffu, gu.lo, u));
       x = gv * sc[u][r] + x;
     }
+  } else if (!s_general) {
+    // B[j][r] = [j = s0 + t_r] - G[s0 + t_r][j] with t_r the selected column
+    const int t = s_sel[r];
+    const df64 gt(__shfl_sync(0xffffffffu, gu.hi, t & 31), __shfl_sync(0xffffffffu, gu.lo, t & 31));
+    if (t >= 0) x = (row == a.s0 + t ? df64(1.f, 0.f) : df64(0.f, 0.f)) - gt;
   } else {
     const int js = row - a.s0;
     if (js >= 0 && js < a.kb) x = sc[js][r];
-    const df64 gu = lane < a.kb ? df_from(Grow[(size_t)lane * N + row]) : df64(0.f, 0.f);
     for (int u = 0; u < a.kb; ++u) {
       const df64 gv(__shfl_sync(0xffffffffu, gu.hi, u), __shfl_sync(0xffffffffu, gu.lo, u));
       x = x - sc[u][r] * gv;

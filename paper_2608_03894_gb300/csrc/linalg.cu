@@ -3,7 +3,8 @@
 // The stabilisation (not in the paper; standard DQMC practice) needs QR
 // factorisations of N x N matrices, explicit Q factors, Q^T applied to a
 // matrix and triangular solves, all in FP64. Blocked Householder QR: a panel
-// of nb columns is factorised by one 8-CTA thread-block cluster whose CTAs
+// of nb columns is factorised by one thread-block cluster (16 CTAs where the
+// part allows it, else 8) whose CTAs
 // each hold a slice of the panel rows in shared memory and combine their
 // partial column dot products through distributed shared memory; the
 // trailing update is two GEMMs with the compact-WY factors V and
@@ -250,6 +251,7 @@ static size_t qr_panel_smem_rows(int rows_per, int nb) {
 }
 
 template <int NB> __global__ void qr_panel_kernel(double *, int, int, int, double *, double *);
+template <int NB> __global__ void qr_panel_df_kernel(double *, int, int, int, double *, double *);
 
 static std::mutex g_qr_mu;
 
@@ -261,6 +263,10 @@ static int qr_cluster_ctas() {
   if (cudaFuncSetAttribute(qr_panel_kernel<64>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
           cudaSuccess &&
       cudaFuncSetAttribute(qr_panel_kernel<32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(qr_panel_df_kernel<64>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(qr_panel_df_kernel<32>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
           cudaSuccess) {
     // the largest panel used here (L = 36, N = 3888) with nb = 64
     const size_t smem = qr_panel_smem_rows((3888 + want - 1) / want, 64);
@@ -445,6 +451,167 @@ __global__ void __launch_bounds__(256)
   cluster.sync();
 }
 
+// The same panel in double-float arithmetic (mixed precision): the column
+// dot products and row updates run as FP32 pairs (~2^-47) on the FP32 units
+// instead of the FP64 pipe (1/64 of the FP32 rate on this part); the
+// reflector's scalars stay FP64. Each column is first scaled by a power of two
+// 2^-e_c (e_c from the cluster-wide largest exponent of the column) so that
+// its entries, their squares and sums stay inside the FP32 range; the
+// reflectors v and tau do not change under a column scaling, and the entries
+// of R are scaled back on the way out. Entries below 2^-126 of their column's
+// largest are dropped.
+__device__ __forceinline__ df64 df_from_scaled(double x, int es) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const int e2 = e - es;
+  if (e == 0 || e2 <= 0) return df64(0.f, 0.f);
+  return df_from(__longlong_as_double((long long)((b & ~(0x7ffull << 52)) | ((unsigned long long)e2 << 52))));
+}
+__device__ __forceinline__ double scale_pow2(double y, int es) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return y;  // zero (or subnormal, which the panel does not produce)
+  const int e2 = e + es;
+  if (e2 <= 0) return 0.0;
+  return __longlong_as_double((long long)((b & ~(0x7ffull << 52)) | ((unsigned long long)e2 << 52)));
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256)
+    qr_panel_df_kernel(double *A, int n, int p, int nc, double *V, double *tau_out) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int ncta = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int m = n - p;
+  const int rows_per = (m + ncta - 1) / ncta;
+  const int lr0 = rank * rows_per;
+  const int myrows = max(0, min(m, lr0 + rows_per) - lr0);
+  constexpr int LDP = NB + 1;
+  extern __shared__ __align__(16) double sm[];
+  df64 *P = reinterpret_cast<df64 *>(sm);   // rows_per x LDP
+  df64 *red = P + (size_t)rows_per * LDP;   // 8 x NB
+  df64 *part = red + 8 * NB;                // 2 x NB
+  df64 *piv = part + 2 * NB;                // 2 x NB
+  df64 *sD = piv + 2 * NB;                  // NB
+  df64 *sy0 = sD + NB;                      // NB
+  df64 *sw = sy0 + NB;                      // NB
+  double *stau = reinterpret_cast<double *>(sw + NB);  // NB
+  __shared__ int ecol[NB], emine[NB];
+  __shared__ df64 ssc[3];                   // tau, beta, scal of the current reflector
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // column scales: the cluster-wide largest exponent of each panel column
+  if (tid < NB) emine[tid] = 0;
+  __syncthreads();
+  for (int e = tid; e < myrows * NB; e += 256) {
+    const int r = e / NB, c = e % NB;
+    if (c < nc) {
+      const double x = A[(size_t)(p + lr0 + r) * n + p + c];
+      atomicMax(&emine[c], (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff));
+    }
+  }
+  cluster.sync();
+  if (tid < NB) {
+    int mx = 0;
+    for (int r2 = 0; r2 < ncta; ++r2) mx = max(mx, cluster.map_shared_rank(emine, r2)[tid]);
+    ecol[tid] = mx > 0 ? mx - 1023 : 0;  // the column's largest entry scales into [1, 2)
+  }
+  __syncthreads();
+  for (int e = tid; e < myrows * NB; e += 256) {
+    const int r = e / NB, c = e % NB;
+    P[r * LDP + c] = (c < nc) ? df_from_scaled(A[(size_t)(p + lr0 + r) * n + p + c], ecol[c]) : df64(0.f, 0.f);
+  }
+  __syncthreads();
+
+  for (int jj = 0; jj < nc; ++jj) {
+    const int buf = jj & 1;
+    const int owner = jj / rows_per;
+    for (int c = lane; c < NB; c += 32) {
+      df64 acc(0.f, 0.f);
+      if (c >= jj && c < nc) {
+        for (int r = warp; r < myrows; r += 8)
+          if (lr0 + r > jj) acc = P[r * LDP + jj] * P[r * LDP + c] + acc;
+      }
+      red[warp * NB + c] = acc;
+    }
+    if (rank == owner)
+      for (int c = tid; c < NB; c += 256) piv[buf * NB + c] = P[(jj - lr0) * LDP + c];
+    __syncthreads();
+    if (tid < NB) {
+      df64 sacc(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) sacc = sacc + red[w * NB + tid];
+      part[buf * NB + tid] = sacc;
+    }
+    // the partial sums and the owner's pivot row become visible cluster-wide;
+    // a CTA can only reuse this buffer parity after the next cluster barrier,
+    // which every CTA reaches after its reads below
+    cluster.sync();
+    {
+      constexpr int NG = 256 / NB;
+      const int c = tid % NB, g = tid / NB;
+      df64 D(0.f, 0.f);
+      for (int r2 = g; r2 < ncta; r2 += NG) D = D + cluster.map_shared_rank(part, r2)[buf * NB + c];
+      red[g * NB + c] = D;
+      if (g == 0) sy0[c] = cluster.map_shared_rank(piv, owner)[buf * NB + c];
+    }
+    __syncthreads();
+    if (tid < NB) {
+      df64 D(0.f, 0.f);
+#pragma unroll
+      for (int g = 0; g < 256 / NB; ++g) D = D + red[g * NB + tid];
+      sD[tid] = D;
+      if (tid == jj) {
+        // the reflector's scalars in FP64, once
+        const double alpha = df_to(sy0[jj]), sigma = df_to(D);
+        double tau = 0.0, beta = alpha, scal = 0.0;
+        if (sigma > 0.0) {
+          const double nrm = sqrt(alpha * alpha + sigma);
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+        ssc[0] = df_from(tau);
+        ssc[1] = df_from(beta);
+        ssc[2] = df_from(scal);
+        stau[jj] = tau;
+      }
+    }
+    __syncthreads();
+    const df64 tau = ssc[0], beta = ssc[1], scal = ssc[2];
+    if (tid < NB) sw[tid] = (tid > jj && tid < nc) ? scal * sD[tid] + sy0[tid] : df64(0.f, 0.f);
+    __syncthreads();
+    for (int r = tid; r < myrows; r += 256) {
+      const int lr = lr0 + r;
+      df64 *row = P + r * LDP;
+      if (lr > jj) {
+        const df64 v = row[jj] * scal;
+        const df64 mtv = -(tau * v);
+        for (int c = jj + 1; c < nc; ++c) row[c] = mtv * sw[c] + row[c];
+        row[jj] = v;
+      } else if (lr == jj) {
+        const df64 mt = -tau;
+        for (int c = jj + 1; c < nc; ++c) row[c] = mt * sw[c] + row[c];
+        row[jj] = beta;
+      }
+    }
+    __syncthreads();
+  }
+
+  // write back R (scaled back by 2^e_c) / V into A and the explicit V
+  for (int e = tid; e < myrows * nc; e += 256) {
+    const int r = e / nc, c = e % nc;
+    const int lr = lr0 + r;
+    const double pv = df_to(P[r * LDP + c]);
+    A[(size_t)(p + lr) * n + p + c] = (lr > c) ? pv : scale_pow2(pv, ecol[c]);
+    V[(size_t)(p + lr) * n + p + c] = (lr > c) ? pv : (lr == c ? 1.0 : 0.0);
+  }
+  if (rank == 0)
+    for (int j = tid; j < nc; j += 256) tau_out[p + j] = stau[j];
+  // no CTA leaves while another may still read its shared memory
+  cluster.sync();
+}
+
 // T (nc x nc, upper triangular, leading dimension NB) of the compact WY form
 // H_0 H_1 ... H_{nc-1} = I - V T V^T. With every tau_j != 0,
 //     T^{-1} = diag(1/tau) + strictly-upper(V^T V)
@@ -508,14 +675,17 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+static thread_local bool t_qr_df = false;
+void set_qr_panel_df(bool on) { t_qr_df = on; }
+
 // Panel p (Householder column loop on one cluster), its Gram matrix V^T V and T.
 template <int NB>
 static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, cudaStream_t st) {
   const int ctas = w.ctas;
   const int rows_per = (n - p + ctas - 1) / ctas;
   const size_t smem = qr_panel_smem_rows(rows_per, NB);
-  cudaError_t e = ensure_smem_attr((const void *)qr_panel_kernel<NB>,
-                                   (int)qr_panel_smem_rows((n + ctas - 1) / ctas, NB));
+  const void *fn = t_qr_df ? (const void *)qr_panel_df_kernel<NB> : (const void *)qr_panel_kernel<NB>;
+  cudaError_t e = ensure_smem_attr(fn, (int)qr_panel_smem_rows((n + ctas - 1) / ctas, NB));
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ctas);
@@ -533,7 +703,8 @@ static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, c
     DQ_KSCOPE(KF_QRPANEL, st);
     // Householder column loop: ~2 m nc^2 flops; the m x nc panel read and written once
     add_work(KF_QRPANEL, 2.0 * (n - p) * (double)nc * nc, 16.0 * (n - p) * (double)nc);
-    e = cudaLaunchKernelEx(&cfg, qr_panel_kernel<NB>, A, n, p, nc, w.V, w.tau);
+    e = t_qr_df ? cudaLaunchKernelEx(&cfg, qr_panel_df_kernel<NB>, A, n, p, nc, w.V, w.tau)
+                : cudaLaunchKernelEx(&cfg, qr_panel_kernel<NB>, A, n, p, nc, w.V, w.tau);
     if (e != cudaSuccess) return e;
   }
   // Gram = V_p^T V_p, then T_p

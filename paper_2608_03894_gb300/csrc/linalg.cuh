@@ -37,6 +37,9 @@ cudaError_t ozgemm(bool ta, bool tb, int M, int N, int K, double alpha, const do
 size_t oz_workspace_bytes(int M, int N, int K);
 void set_oz_workspace(void *ws, size_t bytes, int *exps, size_t nexp);  // exps: >= M + N ints
 void set_gemm_oz(bool on);
+// While set (calling thread), the Householder panels of qr_factor run their
+// column loop in double-float arithmetic (mixed precision).
+void set_qr_panel_df(bool on);
 bool gemm_oz();
 // While set_gemm_oz_tc(true) is in effect for the calling thread, the
 // digit-slice products run on tcgen05 (tensor memory accumulators) instead of

@@ -396,12 +396,14 @@ def test_green_from_scratch_full_size_L24_against_oracle(pkg):
     assert err < 1e-9
 
 
-def test_largest_workload_L36_mixed_sweep_keeps_the_drift_bar(pkg):
-    """The largest workload (L = 36, N = 3888, M = 360, k = 64, n_stab = 8,
-    mixed precision): one sweep keeps every refresh within |dG| <= 1e-6, the
-    field stays +-1, and the acceptance is a proper fraction."""
+@pytest.mark.parametrize("k", [32, 64])
+def test_largest_workload_L36_mixed_sweep_keeps_the_drift_bar(pkg, k):
+    """The largest workload (L = 36, N = 3888, M = 360, n_stab = 8, mixed
+    precision; k = 32 with the tensor-core flush, k = 64 with the double-float
+    flush): one sweep keeps every refresh within |dG| <= 1e-6, the field stays
+    +-1, and the acceptance is a proper fraction."""
     par = dict(L=36, beta=36.0, dtau=0.1, U=-4.0, mu=-1.0)
-    with pkg.DQMC(**par, seed=1, k=64, n_stab=8, precision="mixed") as d:
+    with pkg.DQMC(**par, seed=1, k=k, n_stab=8, precision="mixed") as d:
         d.sweep(1)
         st = d.stats()
         print(f"L=36 mixed: max drift {st['max_drift']:.2e}, acceptance {st['accepted'] / st['proposed']:.3f}")
