@@ -247,7 +247,7 @@ cudaError_t dgemm_fp64(bool ta, bool tb, int M, int N, int K, double alpha, cons
 static int g_qr_ctas = 0;
 
 static size_t qr_panel_smem_rows(int rows_per, int nb) {
-  return ((size_t)rows_per * (nb + 1) + 16 * (size_t)nb + 64) * sizeof(double);
+  return ((size_t)rows_per * (nb + 2) + 16 * (size_t)nb + 64) * sizeof(double);
 }
 
 template <int NB> __global__ void qr_panel_kernel(double *, int, int, int, double *, double *);
@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(256)
   double *sy0 = sD + NB;                     // NB
   double *sw = sy0 + NB;                     // NB
   double *stau = sw + NB;                    // NB
+  double *tvs = stau + NB;                   // rows_per: tau v_r of this CTA's rows
   __shared__ double ssc[3];                  // tau, beta, scal of the current reflector
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -363,13 +364,22 @@ __global__ void __launch_bounds__(256)
   for (int jj = 0; jj < nc; ++jj) {
     const int buf = jj & 1;
     const int owner = jj / rows_per;
-    for (int c = lane; c < NB; c += 32) {
-      double acc = 0.0;
+    // column dot products over this CTA's rows below the diagonal: thread
+    // (column c, row group g) with two independent accumulators
+    {
+      const int c = tid % NB, g = tid / NB;
+      constexpr int NG = 256 / NB;
+      double acc0 = 0.0, acc1 = 0.0;
       if (c >= jj && c < nc) {
-        for (int r = warp; r < myrows; r += 8)
-          if (lr0 + r > jj) acc = fma(P[r * LDP + jj], P[r * LDP + c], acc);
+        const int rs = max(0, jj + 1 - lr0);  // first local row below the diagonal
+        int r = rs + ((g - rs) % NG + NG) % NG;
+        for (; r + NG < myrows; r += 2 * NG) {
+          acc0 = fma(P[r * LDP + jj], P[r * LDP + c], acc0);
+          acc1 = fma(P[(r + NG) * LDP + jj], P[(r + NG) * LDP + c], acc1);
+        }
+        if (r < myrows) acc0 = fma(P[r * LDP + jj], P[r * LDP + c], acc0);
       }
-      red[warp * NB + c] = acc;
+      red[g * NB + c] = acc0 + acc1;
     }
     if (rank == owner)
       for (int c = tid; c < NB; c += 256) piv[buf * NB + c] = P[(jj - lr0) * LDP + c];
@@ -377,7 +387,7 @@ __global__ void __launch_bounds__(256)
     if (tid < NB) {
       double s = 0.0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) s += red[w * NB + tid];
+      for (int w = 0; w < 256 / NB; ++w) s += red[w * NB + tid];
       part[buf * NB + tid] = s;
     }
     // the partial sums and the owner's pivot row become visible cluster-wide;
@@ -419,19 +429,35 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const double tau = ssc[0], beta = ssc[1], scal = ssc[2];
-    if (tid < NB) sw[tid] = (tid > jj && tid < nc) ? sy0[tid] + scal * sD[tid] : 0.0;
-    __syncthreads();
+    // the reflector of each row (v = x scal below the diagonal), tau v, and w
     for (int r = tid; r < myrows; r += 256) {
       const int lr = lr0 + r;
       double *row = P + r * LDP;
       if (lr > jj) {
         const double v = row[jj] * scal;
-        const double tv = tau * v;
-        for (int c = jj + 1; c < nc; ++c) row[c] = fma(-tv, sw[c], row[c]);
+        tvs[r] = tau * v;
         row[jj] = v;
       } else if (lr == jj) {
-        for (int c = jj + 1; c < nc; ++c) row[c] = fma(-tau, sw[c], row[c]);
+        tvs[r] = tau;
         row[jj] = beta;
+      } else {
+        tvs[r] = 0.0;
+      }
+    }
+    if (tid < NB) sw[tid] = (tid > jj && tid < nc) ? sy0[tid] + scal * sD[tid] : 0.0;
+    __syncthreads();
+    // rank-one update of the columns after jj: thread (column offset lane,
+    // row offset warp), the column's w in registers
+    {
+      const int c0 = jj + 1 + lane, c1 = c0 + 32;
+      const double w0 = c0 < nc ? sw[c0] : 0.0, w1 = c1 < nc ? sw[c1] : 0.0;
+      const int rs = max(0, jj - lr0);  // rows at or below the diagonal
+      if (c0 < nc) {
+        for (int r = rs + ((warp - rs) % 8 + 8) % 8; r < myrows; r += 8) {
+          const double t = tvs[r];
+          P[r * LDP + c0] = fma(-t, w0, P[r * LDP + c0]);
+          if (c1 < nc) P[r * LDP + c1] = fma(-t, w1, P[r * LDP + c1]);
+        }
       }
     }
     __syncthreads();
@@ -496,6 +522,7 @@ __global__ void __launch_bounds__(256)
   df64 *sy0 = sD + NB;                      // NB
   df64 *sw = sy0 + NB;                      // NB
   double *stau = reinterpret_cast<double *>(sw + NB);  // NB
+  df64 *tvs = reinterpret_cast<df64 *>(stau + NB);     // rows_per: tau v_r of this CTA's rows
   __shared__ int ecol[NB], emine[NB];
   __shared__ df64 ssc[3];                   // tau, beta, scal of the current reflector
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -526,13 +553,20 @@ __global__ void __launch_bounds__(256)
   for (int jj = 0; jj < nc; ++jj) {
     const int buf = jj & 1;
     const int owner = jj / rows_per;
-    for (int c = lane; c < NB; c += 32) {
-      df64 acc(0.f, 0.f);
+    {
+      const int c = tid % NB, g = tid / NB;
+      constexpr int NG = 256 / NB;
+      df64 acc0(0.f, 0.f), acc1(0.f, 0.f);
       if (c >= jj && c < nc) {
-        for (int r = warp; r < myrows; r += 8)
-          if (lr0 + r > jj) acc = P[r * LDP + jj] * P[r * LDP + c] + acc;
+        const int rs = max(0, jj + 1 - lr0);
+        int r = rs + ((g - rs) % NG + NG) % NG;
+        for (; r + NG < myrows; r += 2 * NG) {
+          acc0 = P[r * LDP + jj] * P[r * LDP + c] + acc0;
+          acc1 = P[(r + NG) * LDP + jj] * P[(r + NG) * LDP + c] + acc1;
+        }
+        if (r < myrows) acc0 = P[r * LDP + jj] * P[r * LDP + c] + acc0;
       }
-      red[warp * NB + c] = acc;
+      red[g * NB + c] = acc0 + acc1;
     }
     if (rank == owner)
       for (int c = tid; c < NB; c += 256) piv[buf * NB + c] = P[(jj - lr0) * LDP + c];
@@ -540,7 +574,7 @@ __global__ void __launch_bounds__(256)
     if (tid < NB) {
       df64 sacc(0.f, 0.f);
 #pragma unroll
-      for (int w = 0; w < 8; ++w) sacc = sacc + red[w * NB + tid];
+      for (int w = 0; w < 256 / NB; ++w) sacc = sacc + red[w * NB + tid];
       part[buf * NB + tid] = sacc;
     }
     // the partial sums and the owner's pivot row become visible cluster-wide;
@@ -579,20 +613,32 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const df64 tau = ssc[0], beta = ssc[1], scal = ssc[2];
-    if (tid < NB) sw[tid] = (tid > jj && tid < nc) ? scal * sD[tid] + sy0[tid] : df64(0.f, 0.f);
-    __syncthreads();
     for (int r = tid; r < myrows; r += 256) {
       const int lr = lr0 + r;
       df64 *row = P + r * LDP;
       if (lr > jj) {
         const df64 v = row[jj] * scal;
-        const df64 mtv = -(tau * v);
-        for (int c = jj + 1; c < nc; ++c) row[c] = mtv * sw[c] + row[c];
+        tvs[r] = -(tau * v);
         row[jj] = v;
       } else if (lr == jj) {
-        const df64 mt = -tau;
-        for (int c = jj + 1; c < nc; ++c) row[c] = mt * sw[c] + row[c];
+        tvs[r] = -tau;
         row[jj] = beta;
+      } else {
+        tvs[r] = df64(0.f, 0.f);
+      }
+    }
+    if (tid < NB) sw[tid] = (tid > jj && tid < nc) ? scal * sD[tid] + sy0[tid] : df64(0.f, 0.f);
+    __syncthreads();
+    {
+      const int c0 = jj + 1 + lane, c1 = c0 + 32;
+      const df64 w0 = c0 < nc ? sw[c0] : df64(0.f, 0.f), w1 = c1 < nc ? sw[c1] : df64(0.f, 0.f);
+      const int rs = max(0, jj - lr0);
+      if (c0 < nc) {
+        for (int r = rs + ((warp - rs) % 8 + 8) % 8; r < myrows; r += 8) {
+          const df64 t = tvs[r];
+          P[r * LDP + c0] = t * w0 + P[r * LDP + c0];
+          if (c1 < nc) P[r * LDP + c1] = t * w1 + P[r * LDP + c1];
+        }
       }
     }
     __syncthreads();
