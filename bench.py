@@ -289,11 +289,66 @@ def metro_microbench(L, k, df, reps=200):
     return {"L": L, "k": k, "arith": "df" if df else "f64", **res}
 
 
+def update_microbench(L, reps=4):
+    """One delayed-update block of the mixed-precision sweep through the C ABI,
+    repeated: the double-float Metropolis block (k = 32) on a G-like block, then
+    the tensor-core flush (digit tiles + tcgen05 update) of that block. Device
+    time per repetition (CUDA events). Also the driver of the ncu captures of
+    these kernels (profiles/)."""
+    import torch
+
+    import paper_2608_03894_gb300 as pkg
+    from dqmc_inputs import random_field, random_green_like
+    k, N = 32, 3 * L * L
+    site0 = min(N - k, (N // 2) // k * k)
+    G0 = torch.as_tensor(random_green_like(N, 3), dtype=torch.float64, device="cuda")
+    s0 = torch.as_tensor(random_field(1, N, seed=3)[0], dtype=torch.int8, device="cuda")
+    g = G0[site0:site0 + k, site0:site0 + k].contiguous()
+    Gcol, Grow = G0[:, site0:site0 + k].contiguous(), G0[site0:site0 + k, :].contiguous()
+    ts = []
+    for _ in range(reps):
+        s = s0.clone()
+        G = G0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        al, be, cnt, st = pkg.ops.metropolis_block(N, site0, k, g, s, 0.6538, 11, 0, 1, 1, df=True)
+        pkg.ops.flush(N, site0, k, G, Gcol, Grow, al, be, cnt, mode="tc")
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1000.0)
+    return {"L": L, "k": k, "accepted": int(cnt.item()), "block_us_incl_op_overheads": [round(t, 1) for t in ts]}
+
+
+def stab_microbench(L):
+    """A short mixed-precision chain at the bench size (beta = L / 10: M = L
+    slices, n_stab = 8): one sweep, whose refreshes run the stabilisation
+    kernels of the full workload (QR panels, digit-slice GEMMs) at N = 3 L^2.
+    Wall time of the sweep. Also the driver of the ncu captures of those
+    kernels (profiles/)."""
+    import time
+
+    import torch
+
+    import paper_2608_03894_gb300 as pkg
+    with pkg.DQMC(L, L / 10.0, 0.1, -4.0, -1.0, seed=1, k=32, n_stab=8, precision="mixed") as d:
+        t = time.time()
+        d.sweep(1)
+        torch.cuda.synchronize()
+        return {"L": L, "M": L, "sweep_s": round(time.time() - t, 3), "max_drift": d.stats()["max_drift"]}
+
+
 def run_micro(args):
     import torch
     torch.cuda.set_device(0)
     peaks, src = load_peaks()
     out = []
+    if args.micro == "update":
+        print(json.dumps({"micro": "update", "results": [update_microbench(args.micro_L)]}), flush=True)
+        return
+    if args.micro == "stab":
+        print(json.dumps({"micro": "stab", "results": [stab_microbench(args.micro_L)]}), flush=True)
+        return
     if args.micro == "metro":
         for df in (False, True):
             out.append(metro_microbench(args.micro_L, 32, df))
@@ -584,10 +639,12 @@ def main():
                     help="sweeps timed for the plain FP64 (and FP32) comparator arms of a mixed "
                          "run; 0 skips them")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--micro", default=None, choices=("prop", "gemm", "metro"),
+    ap.add_argument("--micro", default=None, choices=("prop", "gemm", "metro", "update", "stab"),
                     help="only a microbenchmark: the FFT propagation on a stacked operand larger "
-                         "than L2 (prop; --micro-prec fp32,df,fp64), or the stabilisation GEMM "
-                         "(gemm; --micro-prec f64,df,oz,tc, size --micro-n)")
+                         "than L2 (prop; --micro-prec fp32,df,fp64), the stabilisation GEMM "
+                         "(gemm; --micro-prec f64,df,oz,tc, size --micro-n), one delayed-update "
+                         "block (metro; update: Metropolis + tensor-core flush, --micro-L), or a "
+                         "short chain whose refreshes run the stabilisation kernels (stab, --micro-L)")
     ap.add_argument("--micro-n", type=int, default=1728)
     ap.add_argument("--micro-L", type=int, default=24)
     ap.add_argument("--micro-stack", type=int, default=64)
