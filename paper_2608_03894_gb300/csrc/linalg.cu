@@ -10,6 +10,7 @@
 // trailing update is two GEMMs with the compact-WY factors V and
 // Y = V T^T (Q_panel = I - V T V^T).
 #include <cooperative_groups.h>
+#include <algorithm>
 #include <mutex>
 
 #include "linalg.cuh"
@@ -724,6 +725,83 @@ __global__ void __launch_bounds__(512)
 static thread_local bool t_qr_df = false;
 void set_qr_panel_df(bool on) { t_qr_df = on; }
 
+// Gram matrix V^T V (nc x nc, nc <= 64) of a panel's reflectors in
+// double-float arithmetic (mixed precision), for the compact-WY factor T:
+// the reflector entries are bounded by 1 in magnitude, inside the FP32 range.
+// CTA z sums rows [z R, (z + 1) R) into its own 64 x 64 partial (16 x 16
+// threads, a 4 x 4 block each, rows staged 16 at a time); the partials are
+// then summed in split order (splitk_reduce), so the result is
+// deterministic. Replaces a digit-slice GEMM whose single output tile leaves
+// most of the GPU idle and which costs two operand-slicing launches.
+__global__ void __launch_bounds__(256)
+    gram_df_kernel(const double *__restrict__ V, int ldv, int m, int nc, int rows_per, double *__restrict__ part) {
+  __shared__ float2 sv[16][64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r0 = blockIdx.x * rows_per, r1 = min(m, r0 + rows_per);
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.f;
+  for (int rb = r0; rb < r1; rb += 16) {
+    __syncthreads();
+    for (int e = tid; e < 16 * 64; e += 256) {
+      const int rr = e / 64, c = e % 64;
+      const int r = rb + rr;
+      sv[rr][c] = (r < r1 && c < nc) ? split_df_bits(V[(size_t)r * ldv + c]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int nr = min(16, r1 - rb);
+    for (int rr = 0; rr < nr; ++rr) {
+      float2 x[4], y[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        x[a] = sv[rr][4 * ty + a];
+        y[a] = sv[rr][4 * tx + a];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          // double-float multiply-add (FMA residual product, TwoSum accumulation)
+          const float pp = x[a].x * y[b].x;
+          float e = fmaf(x[a].x, y[b].x, -pp);
+          e = fmaf(x[a].x, y[b].y, e);
+          e = fmaf(x[a].y, y[b].x, e);
+          const float t = sh[a][b] + pp;
+          const float z = t - sh[a][b];
+          const float err = (sh[a][b] - (t - z)) + (pp - z);
+          sh[a][b] = t;
+          sl[a][b] += err + e;
+        }
+    }
+  }
+  double *out = part + (size_t)blockIdx.x * nc * nc;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 4 * ty + a, j = 4 * tx + b;
+      if (i < nc && j < nc) out[(size_t)i * nc + j] = f2d_bits(sh[a][b]) + f2d_bits(sl[a][b]);
+    }
+}
+
+static cudaError_t gram_df(const double *V, int ldv, int m, int nc, double *G, int ldg, cudaStream_t st) {
+  const int splits = std::max(1, std::min(64, (m + 15) / 16));
+  const int rows_per = (m + splits - 1) / splits;
+  double *part = splitk_partials(splits, nc, nc);
+  if (!part)  // a panel of at most 16 rows (or no partials workspace): FP64
+    return dgemm_fp64(true, false, nc, nc, m, 1.0, V, ldv, V, ldv, 0.0, G, ldg, nullptr, nullptr, st);
+  {
+    DQ_KSCOPE(KF_GEMM, st);
+    add_work(KF_GEMM, 2.0 * m * (double)nc * nc, 8.0 * m * (double)nc);
+    gram_df_kernel<<<splits, 256, 0, st>>>(V, ldv, m, nc, rows_per, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return splitk_reduce(part, splits, nc, nc, 0.0, G, ldg, st);
+}
+
 // Panel p (Householder column loop on one cluster), its Gram matrix V^T V and T.
 template <int NB>
 static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, cudaStream_t st) {
@@ -756,11 +834,73 @@ static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, c
   // Gram = V_p^T V_p, then T_p
   const int m = n - p;
   const double *Vp = w.V + (size_t)p * n + p;
-  e = dgemm(true, false, nc, nc, m, 1.0, Vp, n, Vp, n, 0.0, w.Gram, w.nb, nullptr, nullptr, st);
+  e = gemm_oz() ? gram_df(Vp, n, m, nc, w.Gram, w.nb, st)
+                : dgemm(true, false, nc, nc, m, 1.0, Vp, n, Vp, n, 0.0, w.Gram, w.nb, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   DQ_KSCOPE(KF_STABAUX, st);
   qr_t_kernel<<<1, 512, 0, st>>>(w.Gram, w.nb, w.tau + p, nc, w.nb,
                                                                    w.T + (size_t)(p / w.nb) * w.nb * w.nb);
+  return cudaGetLastError();
+}
+
+// W2 = op(T) W (nc x ncols, nc <= 64, T nc x nc with leading dimension ldt)
+// in double-float arithmetic (mixed precision): the middle product of a
+// block reflector, 64 x ncols x 64, too small to fill the GPU as a digit-slice
+// GEMM. The columns of W carry the graded scales of the matrix the reflector
+// is applied to, so each column is scaled by a power of two (its largest
+// exponent) into the FP32 range before the product and scaled back after;
+// T's entries are bounded. CTA per 16 columns, thread (column, 4 rows).
+template <bool TT>
+__global__ void __launch_bounds__(256)
+    tw_df_kernel(const double *__restrict__ T, int ldt, const double *__restrict__ W, int ldw, int nc, int ncols,
+                 double *__restrict__ W2, int ldw2) {
+  __shared__ df64 st[64][65];   // op(T)[i][k]
+  __shared__ df64 sw[64][16];   // scaled W[k][j0 + c]
+  __shared__ int emax[16];
+  const int tid = threadIdx.x, c = tid & 15, ig = tid >> 4;  // ig: rows 4 ig .. 4 ig + 3
+  const int j0 = blockIdx.x * 16, j = j0 + c;
+  if (tid < 16) emax[tid] = 0;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int i = e / 64, k = e % 64;
+    const double t = (i < nc && k < nc) ? (TT ? T[(size_t)k * ldt + i] : T[(size_t)i * ldt + k]) : 0.0;
+    st[i][k] = df_from(t);
+  }
+  __syncthreads();
+  for (int e = tid; e < 64 * 16; e += 256) {
+    const int k = e / 16, cc = e % 16;
+    if (k < nc && j0 + cc < ncols) {
+      const double w = W[(size_t)k * ldw + j0 + cc];
+      atomicMax(&emax[cc], (int)(((unsigned long long)__double_as_longlong(w) >> 52) & 0x7ff));
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 64 * 16; e += 256) {
+    const int k = e / 16, cc = e % 16;
+    const int es = emax[cc] > 0 ? emax[cc] - 1023 : 0;
+    sw[k][cc] = (k < nc && j0 + cc < ncols) ? df_from_scaled(W[(size_t)k * ldw + j0 + cc], es) : df64(0.f, 0.f);
+  }
+  __syncthreads();
+  if (j >= ncols) return;
+  const int es = emax[c] > 0 ? emax[c] - 1023 : 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = 4 * ig + a;
+    if (i >= nc) continue;
+    df64 acc(0.f, 0.f);
+    for (int k = 0; k < nc; ++k) acc = st[i][k] * sw[k][c] + acc;
+    W2[(size_t)i * ldw2 + j] = scale_pow2(df_to(acc), es);
+  }
+}
+
+static cudaError_t tw_df(bool trans_t, const double *T, int ldt, const double *W, int ldw, int nc, int ncols,
+                         double *W2, int ldw2, cudaStream_t st) {
+  DQ_KSCOPE(KF_GEMM, st);
+  add_work(KF_GEMM, 2.0 * nc * (double)nc * ncols, 8.0 * (2.0 * nc * (double)ncols + (double)nc * nc));
+  const int grid = (ncols + 15) / 16;
+  if (trans_t)
+    tw_df_kernel<true><<<grid, 256, 0, st>>>(T, ldt, W, ldw, nc, ncols, W2, ldw2);
+  else
+    tw_df_kernel<false><<<grid, 256, 0, st>>>(T, ldt, W, ldw, nc, ncols, W2, ldw2);
   return cudaGetLastError();
 }
 
@@ -773,8 +913,9 @@ static cudaError_t apply_block_reflector(const QRWork &w, int p, int nc, bool tr
   cudaError_t e = dgemm(true, false, nc, ncols, m, 1.0, Vp, n, B, ldb, 0.0, w.W, ncols, nullptr,
                         nullptr, st);
   if (e != cudaSuccess) return e;
-  e = dgemm(trans_t, false, nc, ncols, nc, 1.0, Tp, w.nb, w.W, ncols, 0.0, w.W2, ncols, nullptr,
-            nullptr, st);
+  e = gemm_oz() ? tw_df(trans_t, Tp, w.nb, w.W, ncols, nc, ncols, w.W2, ncols, st)
+                : dgemm(trans_t, false, nc, ncols, nc, 1.0, Tp, w.nb, w.W, ncols, 0.0, w.W2, ncols, nullptr,
+                        nullptr, st);
   if (e != cudaSuccess) return e;
   return dgemm(false, false, m, ncols, nc, -1.0, Vp, n, w.W2, ncols, 1.0, B, ldb, nullptr, nullptr,
                st, 1);
