@@ -157,6 +157,15 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                powers of two, reflector scalars in FP64 (default 0: the
  *                panel is bound by barrier latency, not by the FP64 pipe, and
  *                this gains ~2% of an L = 24 sweep for ~2x the drift);
+ *   "refl_gram"  with stab_gemm = 2: the Gram matrix V^T V of each block
+ *                reflector of the QR, whose digit-slice GEMM leaves most of
+ *                the GPU idle: 0 = digit slices, 1 = a parallel FP64 kernel
+ *                (default), 2 = a parallel double-float kernel (its error costs
+ *                the reflectors' orthogonality: L = 36 drift above 1e-6);
+ *   "refl_tw"    with stab_gemm = 2: op(T) W of each block reflector as a
+ *                column-scaled double-float kernel (1) instead of digit slices
+ *                (0, default; 1 is ~3% faster per L = 24 sweep but drifts to
+ *                ~1e-6 at L = 24 and 1.9e-6 at L = 36 over a few sweeps);
  *   "stab_gemm"  stabilisation GEMMs: 0 = FP64, 1 = double-float, 2 = exact
  *                7-bit digit slices on the bf16 tensor cores (default 2);
  *   "tc_gemm"    with stab_gemm = 2: 1 (default) = the digit-slice products

@@ -223,7 +223,10 @@ struct dqmc_ctx {
   int tc_gemm = 1;    // mixed, digit slices: tcgen05 GEMM (else the mma.sync one)
   int flush_tc = 1;   // mixed, k = 32: rank-m flush as digit slices on tcgen05 (else double-float)
   int df_panel = 0;   // mixed: Householder panel column loop in double-float arithmetic
+  int refl_gram = 1;  // mixed: Gram matrix of each block reflector (0 digit slices, 1 parallel FP64, 2 double-float)
+  int refl_tw = 0;    // mixed: op(T) W of each block reflector (0 digit slices, 1 double-float)
   void *tcws = nullptr;  // its digit tiles and row exponents
+  int *tcperm = nullptr;  // 2 x k: the accepted sites of a block (block parity), for the digit tiles
   bool cholqr = false;  // the sweep's stabilisation uses CholeskyQR2 (resolved at allocation)
   unsigned gemm_sites = 0xffffffffu;  // mixed: GEMM call sites (GemmSite bits) that use stab_gemm
   unsigned gemm_df_sites = 0u;        // mixed: of those, the sites that use double-float products
@@ -378,6 +381,7 @@ dqmc_status ensure_alloc(dqmc_ctx *c) {
     const size_t b = flush_tc_workspace_bytes(N);
     DQ_CHECK(ctx_alloc(c, &c->tcws, b));
     CK(cudaMemsetAsync(c->tcws, 0, b, c->stream));
+    DQ_CHECK(ctx_alloc_n(c, &c->tcperm, 2 * (size_t)c->k));
   }
   DQ_CHECK(ctx_alloc_n(c, &c->acc, 4));
   DQ_CHECK(ctx_alloc_n(c, &c->status, 4));
@@ -550,13 +554,15 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
   if constexpr (std::is_same<T, double>::value) {
     if (df && c->tcws && K == 32) {
       // tensor-core flush. Per block on the context's stream: the digit
-      // tiles (which also form the next block's rows of A), the look-ahead
-      // G'[S', S'], then the flush, which gathers the next block's rows and
-      // columns; the next block's Metropolis runs on the side stream between
-      // the look-ahead and the next digit tiles, beside the flush.
+      // tiles (whose warps for the next block's rows of A also form the
+      // look-ahead G'[S', S'] from the pre-flush G), then the flush, which
+      // gathers the next block's rows and columns; the next block's
+      // Metropolis runs on the side stream between the digit tiles and the
+      // next block's, beside the flush.
       ma.s0 = 0;
       ma.kb = std::min(K, N);
       ma.ld_g = N;
+      ma.perm = c->tcperm;
       CK(launch_metropolis(ma, Gr[0], false, s, forced, c->coef_a, c->coef_b, c->acc, c->status, c->total_acc,
                            c->stream, dfm));
       for (int b = 0; b < nblk; ++b) {
@@ -574,10 +580,10 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
         fa.ldc = K;
         fa.ldb = K;
         fa.lda = K;
-        float2 *Anext = fa.nkb > 0 ? static_cast<float2 *>(c->Abuf) : nullptr;
-        CK(launch_flush_tc_prep(fa, Gc[par], Gr[par], al, be, acc, c->tcws, Anext, c->stream));
+        // the digit tiles, and the next block's G'[S', S'] from the pre-flush G
+        CK(launch_flush_tc_prep(fa, Gc[par], Gr[par], al, be, acc, c->tcws, nullptr, c->stream, c->tcperm + par * K, G,
+                                fa.nkb > 0 ? c->gnext : nullptr));
         if (fa.nkb > 0) {
-          CK(launch_lookahead_g<double>(K, fa, G, c->Abuf, true, Gr[par], be, acc, c->gnext, c->stream));
           cudaStream_t ms = c->stream;
           if (c->pipeline) {
             CK(cudaEventRecord(c->ev_fork, c->stream));
@@ -588,6 +594,7 @@ dqmc_status update_slice_t(dqmc_ctx *c, T *G, int l, int pas, const uint8_t *for
           mn.s0 = fa.ns0;
           mn.kb = fa.nkb;
           mn.ld_g = fa.nkb;
+          mn.perm = c->tcperm + (par ^ 1) * K;
           CK(launch_metropolis(mn, c->gnext, false, s, forced ? forced + fa.ns0 : nullptr,
                                c->coef_a + (par ^ 1) * KK, c->coef_b + (par ^ 1) * KK, c->acc + (par ^ 1),
                                c->status, c->total_acc, ms, dfm));
@@ -794,6 +801,7 @@ struct GemmModeScope {
     set_splitk_workspace(c->skws, splitk_ws_doubles());
     if (c->precision != 1) return;
     set_qr_panel_df(c->df_panel != 0);
+    set_reflector_modes(c->refl_gram, c->refl_tw);
     if (c->stab_gemm == 1 && c->dfws) {
       set_df_workspace(c->dfws, c->dfws_elems);
       set_gemm_df(true);
@@ -812,6 +820,7 @@ struct GemmModeScope {
   ~GemmModeScope() {
     set_splitk_workspace(nullptr, 0);
     set_qr_panel_df(false);
+    set_reflector_modes(0, 0);
     set_gemm_df(false);
     set_gemm_oz(false);
     set_gemm_oz_tc(false);
@@ -1116,6 +1125,11 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
     c->tc_gemm = v != 0.0;
   } else if (k == "df_panel") {
     c->df_panel = v != 0.0;
+  } else if (k == "refl_gram") {
+    if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "refl_gram must be 0, 1 or 2");
+    c->refl_gram = (int)v;
+  } else if (k == "refl_tw") {
+    c->refl_tw = v != 0.0;
   } else if (k == "flush_tc") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     c->flush_tc = v != 0.0;

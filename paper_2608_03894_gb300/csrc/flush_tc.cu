@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(256)
                          const double *__restrict__ Grow, const double *__restrict__ beta,
                          const int *__restrict__ accept_count, unsigned short *__restrict__ Ud,
                          unsigned short *__restrict__ Vd, int *__restrict__ eU, int *__restrict__ eV,
-                         int nblk_a, float2 *__restrict__ Anext) {
+                         int nblk_a, float2 *__restrict__ Anext, const int *__restrict__ perm,
+                         const double *__restrict__ G, double *__restrict__ gnext) {
   __shared__ df64 sc[FT_K][FT_K + 1];  // sc[u][r] = coefficient [r][u]
   __shared__ int s_sel[FT_K];          // B rows: the column of row r's single 1 (-1: none)
   __shared__ int s_nz[FT_K], s_nnz, s_general;  // A rows: the columns with a nonzero coefficient
@@ -118,12 +119,22 @@ __global__ void __launch_bounds__(256)
       s_nnz = 0;
       s_general = 0;
     }
-    for (int e = threadIdx.x; e < FT_K * FT_K; e += 256) {
-      const int r = e / FT_K, u = e % FT_K;
-      sc[u][r] = (r < m && u < a.kb) ? df_from(coef[r * ld + u]) : df64(0.f, 0.f);
+    // with the accepted sites given, beta is a selector (not staged) and
+    // alpha's nonzero columns are those sites
+    if (isa || !perm)
+      for (int e = threadIdx.x; e < FT_K * FT_K; e += 256) {
+        const int r = e / FT_K, u = e % FT_K;
+        sc[u][r] = (r < m && u < a.kb) ? df_from(coef[r * ld + u]) : df64(0.f, 0.f);
+      }
+    if (perm && threadIdx.x < FT_K) {
+      const int t = (int)threadIdx.x < m ? perm[threadIdx.x] : -1;
+      s_sel[threadIdx.x] = t;
+      s_nz[threadIdx.x] = t < 0 ? 0 : t;
     }
     __syncthreads();
-    if (warp == 0) {
+    if (perm) {
+      if (threadIdx.x == 0) s_nnz = m;
+    } else if (warp == 0) {
       // column u of the coefficients holds a nonzero (A), or row r = lane is a
       // selector: one entry equal to 1, the rest 0 (B)
       bool nz = false;
@@ -174,6 +185,18 @@ __global__ void __launch_bounds__(256)
   }
   // the next block's rows of A (double-float pairs, row stride 32) for the look-ahead
   if (isa && Anext && row - a.ns0 >= 0 && row - a.ns0 < a.nkb) Anext[(size_t)row * FT_K + r] = make_float2(x.hi, x.lo);
+  // ... or the look-ahead itself: G'[i][j] = G[i][j] + sum_q A[i][q] G[S_{P_q}][j] for the
+  // next block's rows i and columns j (beta's row q selects P_q; j is outside this block)
+  if (isa && perm && gnext && row - a.ns0 >= 0 && row - a.ns0 < a.nkb) {
+    df64 acc(0.f, 0.f);
+    for (int q = 0; q < m; ++q) {
+      const df64 aq(__shfl_sync(0xffffffffu, x.hi, q), __shfl_sync(0xffffffffu, x.lo, q));
+      const double gq = lane < a.nkb ? Grow[(size_t)s_sel[q] * N + a.ns0 + lane] : 0.0;
+      acc = aq * df_from(gq) + acc;
+    }
+    if (lane < a.nkb)
+      gnext[(size_t)(row - a.ns0) * a.nkb + lane] = G[(size_t)row * N + a.ns0 + lane] + df_to(acc);
+  }
   // row exponent: |x| < 2^ex for every entry (|hi| + |lo| < 2^(e(hi) + 1))
   const unsigned int hb = (unsigned int)__float_as_int(x.hi);
   const int ef = (hb & 0x7fffffff) ? (int)((hb >> 23) & 0xff) : 0;
@@ -380,7 +403,8 @@ __global__ void __launch_bounds__(FT_THREADS, 2)
 }
 
 cudaError_t launch_flush_tc_prep(const FlushArgs &a, const double *Gcol, const double *Grow, const double *alpha,
-                                 const double *beta, const int *acc, void *ws, float2 *Anext, cudaStream_t st) {
+                                 const double *beta, const int *acc, void *ws, float2 *Anext, cudaStream_t st,
+                                 const int *perm, const double *G, double *gnext) {
   if (a.kb < 1 || a.kb > FT_K || a.nkb > FT_K) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return cudaErrorInvalidValue;
   const int N = a.N;
@@ -392,7 +416,8 @@ cudaError_t launch_flush_tc_prep(const FlushArgs &a, const double *Gcol, const d
   DQ_KSCOPE(KF_BLOCKAUX, st);
   add_work(KF_BLOCKAUX, 4.0 * N * (double)FT_K * a.kb, 8.0 * N * (double)(2 * a.kb + 2 * FT_K));
   const int nblk = (N + 7) / 8;
-  flush_tc_prep_kernel<<<2 * nblk, 256, 0, st>>>(a, Gcol, alpha, Grow, beta, acc, Ud, Vd, eU, eV, nblk, Anext);
+  flush_tc_prep_kernel<<<2 * nblk, 256, 0, st>>>(a, Gcol, alpha, Grow, beta, acc, Ud, Vd, eU, eV, nblk, Anext,
+                                                 perm, G, gnext);
   return cudaGetLastError();
 }
 

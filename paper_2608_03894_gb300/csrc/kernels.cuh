@@ -35,6 +35,7 @@ struct MetroArgs {
   uint32_t k0, k1;       // Philox key (seed)
   uint32_t c2, c3;       // counter words 2 (2*sweep + pass) and 3 (chain | domain << 24)
   int slice0;            // counter word 1 (0-based slice)
+  int *perm = nullptr;   // k <= 32: if set, the accepted sites (block-relative, in order), -1 after
 };
 // Decisions and Woodbury coefficients of one block (see update.cu), in FP64
 // or (df) double-float arithmetic. reserve_smem: shared memory to claim
@@ -93,8 +94,13 @@ bool flush_tc_timed_out(cudaStream_t st);
 // The two launches of launch_flush_tc: the digit tiles (and, when Anext is
 // not NULL, the next block's rows of A as double-float pairs, Anext[i * 32 +
 // r] for a.ns0 <= i < a.ns0 + a.nkb, for the look-ahead), then the update.
+// With perm (the accepted sites of the block, as the Metropolis block writes
+// them; beta then has its selector form), the tiles kernel skips the scan of
+// the coefficients and, given G (pre-flush) and gnext, also writes the next
+// block's G'[S', S'] (a.nkb x a.nkb, row stride a.nkb).
 cudaError_t launch_flush_tc_prep(const FlushArgs &a, const double *Gcol, const double *Grow, const double *alpha,
-                                 const double *beta, const int *acc, void *ws, float2 *Anext, cudaStream_t st);
+                                 const double *beta, const int *acc, void *ws, float2 *Anext, cudaStream_t st,
+                                 const int *perm = nullptr, const double *G = nullptr, double *gnext = nullptr);
 cudaError_t launch_flush_tc_update(const FlushArgs &a, double *G, const int *acc, void *ws, double *Gcol_next,
                                    double *Grow_next, cudaStream_t st);
 

@@ -724,17 +724,61 @@ __global__ void __launch_bounds__(512)
 
 static thread_local bool t_qr_df = false;
 void set_qr_panel_df(bool on) { t_qr_df = on; }
+static thread_local int t_refl_gram = 0, t_refl_tw = 0;
+void set_reflector_modes(int gram, int tw) {
+  t_refl_gram = gram;
+  t_refl_tw = tw;
+}
 
-// Gram matrix V^T V (nc x nc, nc <= 64) of a panel's reflectors in
-// double-float arithmetic (mixed precision), for the compact-WY factor T:
-// the reflector entries are bounded by 1 in magnitude, inside the FP32 range.
-// CTA z sums rows [z R, (z + 1) R) into its own 64 x 64 partial (16 x 16
-// threads, a 4 x 4 block each, rows staged 16 at a time); the partials are
-// then summed in split order (splitk_reduce), so the result is
-// deterministic. Replaces a digit-slice GEMM whose single output tile leaves
-// most of the GPU idle and which costs two operand-slicing launches.
+// Gram matrix V^T V (nc x nc, nc <= 64) of a panel's reflectors, for the
+// compact-WY factor T, in FP64 or in double-float arithmetic (the reflector
+// entries are bounded by 1 in magnitude, inside the FP32 range). CTA z sums
+// rows [z R, (z + 1) R) into its own 64 x 64 partial (16 x 16 threads, a
+// 4 x 4 block each, rows staged 16 at a time); the partials are then summed
+// in split order (splitk_reduce), so the result is deterministic. Replaces a
+// digit-slice GEMM whose single output tile leaves most of the GPU idle and
+// which costs two operand-slicing launches. The double-float form loses
+// orthogonality of the block reflectors at the 2^-47 level, which shows in
+// the drift at L = 36.
+template <bool DF>
 __global__ void __launch_bounds__(256)
-    gram_df_kernel(const double *__restrict__ V, int ldv, int m, int nc, int rows_per, double *__restrict__ part) {
+    gram_kernel(const double *__restrict__ V, int ldv, int m, int nc, int rows_per, double *__restrict__ part) {
+  if constexpr (!DF) {
+    // FP64: thread (ty, tx) owns the 4 x 4 block; rows staged 16 at a time
+    __shared__ double sd[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int r0 = blockIdx.x * rows_per, r1 = min(m, r0 + rows_per);
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int rb = r0; rb < r1; rb += 16) {
+      __syncthreads();
+      for (int e = tid; e < 16 * 64; e += 256) {
+        const int rr = e / 64, c = e % 64;
+        const int r = rb + rr;
+        sd[rr][c] = (r < r1 && c < nc) ? V[(size_t)r * ldv + c] : 0.0;
+      }
+      __syncthreads();
+      const int nr = min(16, r1 - rb);
+      for (int rr = 0; rr < nr; ++rr) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(sd[rr][4 * ty + a], sd[rr][4 * tx + b], acc[a][b]);
+      }
+    }
+    double *out = part + (size_t)blockIdx.x * nc * nc;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = 4 * ty + a, j = 4 * tx + b;
+        if (i < nc && j < nc) out[(size_t)i * nc + j] = acc[a][b];
+      }
+    return;
+  }
   __shared__ float2 sv[16][64];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int r0 = blockIdx.x * rows_per, r1 = min(m, r0 + rows_per);
@@ -786,8 +830,10 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-static cudaError_t gram_df(const double *V, int ldv, int m, int nc, double *G, int ldg, cudaStream_t st) {
-  const int splits = std::max(1, std::min(64, (m + 15) / 16));
+// df = false: FP64 products on 256 CTAs (the partials summed in order), df =
+// true: double-float on 64
+static cudaError_t gram_par(bool df, const double *V, int ldv, int m, int nc, double *G, int ldg, cudaStream_t st) {
+  const int splits = std::max(1, std::min(df ? 64 : 256, (m + (df ? 15 : 3)) / (df ? 16 : 4)));
   const int rows_per = (m + splits - 1) / splits;
   double *part = splitk_partials(splits, nc, nc);
   if (!part)  // a panel of at most 16 rows (or no partials workspace): FP64
@@ -795,7 +841,10 @@ static cudaError_t gram_df(const double *V, int ldv, int m, int nc, double *G, i
   {
     DQ_KSCOPE(KF_GEMM, st);
     add_work(KF_GEMM, 2.0 * m * (double)nc * nc, 8.0 * m * (double)nc);
-    gram_df_kernel<<<splits, 256, 0, st>>>(V, ldv, m, nc, rows_per, part);
+    if (df)
+      gram_kernel<true><<<splits, 256, 0, st>>>(V, ldv, m, nc, rows_per, part);
+    else
+      gram_kernel<false><<<splits, 256, 0, st>>>(V, ldv, m, nc, rows_per, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -834,7 +883,7 @@ static cudaError_t launch_qr_panel(double *A, int n, int p, int nc, QRWork &w, c
   // Gram = V_p^T V_p, then T_p
   const int m = n - p;
   const double *Vp = w.V + (size_t)p * n + p;
-  e = gemm_oz() ? gram_df(Vp, n, m, nc, w.Gram, w.nb, st)
+  e = (gemm_oz() && t_refl_gram) ? gram_par(t_refl_gram == 2, Vp, n, m, nc, w.Gram, w.nb, st)
                 : dgemm(true, false, nc, nc, m, 1.0, Vp, n, Vp, n, 0.0, w.Gram, w.nb, nullptr, nullptr, st);
   if (e != cudaSuccess) return e;
   DQ_KSCOPE(KF_STABAUX, st);
@@ -913,7 +962,7 @@ static cudaError_t apply_block_reflector(const QRWork &w, int p, int nc, bool tr
   cudaError_t e = dgemm(true, false, nc, ncols, m, 1.0, Vp, n, B, ldb, 0.0, w.W, ncols, nullptr,
                         nullptr, st);
   if (e != cudaSuccess) return e;
-  e = gemm_oz() ? tw_df(trans_t, Tp, w.nb, w.W, ncols, nc, ncols, w.W2, ncols, st)
+  e = (gemm_oz() && t_refl_tw) ? tw_df(trans_t, Tp, w.nb, w.W, ncols, nc, ncols, w.W2, ncols, st)
                 : dgemm(trans_t, false, nc, ncols, nc, 1.0, Tp, w.nb, w.W, ncols, 0.0, w.W2, ncols, nullptr,
                         nullptr, st);
   if (e != cudaSuccess) return e;

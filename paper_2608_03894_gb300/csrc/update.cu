@@ -434,6 +434,7 @@ __global__ void __launch_bounds__(kMetroCta)
     if (i < m && lane < m) alpha_out[lane * a.K + s_P[i]] = MM::to(x[q]);
   }
   if (tid < m) beta_out[tid * a.K + s_P[tid]] = 1.0;
+  if (a.perm && tid < a.K) a.perm[tid] = tid < m ? s_P[tid] : -1;
   if (tid == 0) {
     *accept_count = m;
     if (failed) *status = 1;

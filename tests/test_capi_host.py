@@ -81,6 +81,10 @@ def test_create_and_destroy_without_gpu_work(lib):
     assert lib.dqmc_set_option(h, b"tc_gemm", 0.0) == 0
     assert lib.dqmc_set_option(h, b"df_metro", 0.0) == 0
     assert lib.dqmc_set_option(h, b"flush_tc", 0.0) == 0
+    assert lib.dqmc_set_option(h, b"refl_gram", 2.0) == 0
+    assert lib.dqmc_set_option(h, b"refl_gram", 3.0) == 1
+    assert lib.dqmc_set_option(h, b"refl_tw", 1.0) == 0
+    assert lib.dqmc_set_option(h, b"df_panel", 1.0) == 0
     assert lib.dqmc_set_option(h, b"metro_reserve", 224 * 1024 + 1.0) == 1
     lib.dqmc_destroy(h)
 
