@@ -224,7 +224,7 @@ struct dqmc_ctx {
   int flush_tc = 1;   // mixed, k = 32: rank-m flush as digit slices on tcgen05 (else double-float)
   int df_panel = 0;   // mixed: Householder panel column loop in double-float arithmetic
   int refl_gram = 1;  // mixed: Gram matrix of each block reflector (0 digit slices, 1 parallel FP64, 2 double-float)
-  int refl_tw = 0;    // mixed: op(T) W of each block reflector (0 digit slices, 1 double-float)
+  int refl_tw = 1;    // mixed: op(T) W of each block reflector (0 digit slices, 1 parallel FP64, 2 double-float)
   void *tcws = nullptr;  // its digit tiles and row exponents
   int *tcperm = nullptr;  // 2 x k: the accepted sites of a block (block parity), for the digit tiles
   bool cholqr = false;  // the sweep's stabilisation uses CholeskyQR2 (resolved at allocation)
@@ -1129,7 +1129,8 @@ dqmc_status dqmc_set_option(dqmc_ctx *c, const char *key, double v) try {
     if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "refl_gram must be 0, 1 or 2");
     c->refl_gram = (int)v;
   } else if (k == "refl_tw") {
-    c->refl_tw = v != 0.0;
+    if (v != 0.0 && v != 1.0 && v != 2.0) return fail(DQMC_EINVAL, "refl_tw must be 0, 1 or 2");
+    c->refl_tw = (int)v;
   } else if (k == "flush_tc") {
     if (c->allocated) return fail(DQMC_ESTATE, "option '" + k + "' is fixed after the first sweep");
     c->flush_tc = v != 0.0;

@@ -941,15 +941,62 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-static cudaError_t tw_df(bool trans_t, const double *T, int ldt, const double *W, int ldw, int nc, int ncols,
-                         double *W2, int ldw2, cudaStream_t st) {
+// The same product in FP64, on a CTA per 8 columns (216 CTAs for 1728
+// columns, so the whole GPU's FP64 pipes share the 2 nc^2 ncols flops): op(T)
+// staged in shared memory (read along T's rows, stored transposed when
+// op = T^T), thread (column c, rows 2 ig and 2 ig + 1), the sum over k in
+// order with fused multiply-adds.
+template <bool TT>
+__global__ void __launch_bounds__(256)
+    tw_fp64_kernel(const double *__restrict__ T, int ldt, const double *__restrict__ W, int ldw, int nc, int ncols,
+                   double *__restrict__ W2, int ldw2) {
+  __shared__ double st[64][65];  // op(T)[i][k]
+  __shared__ double sw[64][8];   // W[k][j0 + c]
+  const int tid = threadIdx.x, c = tid & 7, ig = tid >> 3;
+  const int j0 = blockIdx.x * 8, j = j0 + c;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int r = e / 64, q = e % 64;  // T[r][q]
+    const double t = (r < nc && q < nc) ? T[(size_t)r * ldt + q] : 0.0;
+    if (TT)
+      st[q][r] = t;
+    else
+      st[r][q] = t;
+  }
+  for (int e = tid; e < 64 * 8; e += 256) {
+    const int k = e / 8, cc = e % 8;
+    sw[k][cc] = (k < nc && j0 + cc < ncols) ? W[(size_t)k * ldw + j0 + cc] : 0.0;
+  }
+  __syncthreads();
+  if (j >= ncols) return;
+  const int i0 = 2 * ig, i1 = i0 + 1;
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int k = 0; k < nc; ++k) {
+    const double w = sw[k][c];
+    acc0 = fma(st[i0][k], w, acc0);
+    acc1 = fma(st[i1][k], w, acc1);
+  }
+  if (i0 < nc) W2[(size_t)i0 * ldw2 + j] = acc0;
+  if (i1 < nc) W2[(size_t)i1 * ldw2 + j] = acc1;
+}
+
+// W2 = op(T) W by the double-float (df) or the FP64 kernel
+static cudaError_t tw_par(bool df, bool trans_t, const double *T, int ldt, const double *W, int ldw, int nc,
+                          int ncols, double *W2, int ldw2, cudaStream_t st) {
   DQ_KSCOPE(KF_GEMM, st);
   add_work(KF_GEMM, 2.0 * nc * (double)nc * ncols, 8.0 * (2.0 * nc * (double)ncols + (double)nc * nc));
-  const int grid = (ncols + 15) / 16;
-  if (trans_t)
-    tw_df_kernel<true><<<grid, 256, 0, st>>>(T, ldt, W, ldw, nc, ncols, W2, ldw2);
-  else
-    tw_df_kernel<false><<<grid, 256, 0, st>>>(T, ldt, W, ldw, nc, ncols, W2, ldw2);
+  if (df) {
+    const int grid = (ncols + 15) / 16;
+    if (trans_t)
+      tw_df_kernel<true><<<grid, 256, 0, st>>>(T, ldt, W, ldw, nc, ncols, W2, ldw2);
+    else
+      tw_df_kernel<false><<<grid, 256, 0, st>>>(T, ldt, W, ldw, nc, ncols, W2, ldw2);
+  } else {
+    const int grid = (ncols + 7) / 8;
+    if (trans_t)
+      tw_fp64_kernel<true><<<grid, 256, 0, st>>>(T, ldt, W, ldw, nc, ncols, W2, ldw2);
+    else
+      tw_fp64_kernel<false><<<grid, 256, 0, st>>>(T, ldt, W, ldw, nc, ncols, W2, ldw2);
+  }
   return cudaGetLastError();
 }
 
@@ -962,7 +1009,7 @@ static cudaError_t apply_block_reflector(const QRWork &w, int p, int nc, bool tr
   cudaError_t e = dgemm(true, false, nc, ncols, m, 1.0, Vp, n, B, ldb, 0.0, w.W, ncols, nullptr,
                         nullptr, st);
   if (e != cudaSuccess) return e;
-  e = (gemm_oz() && t_refl_tw) ? tw_df(trans_t, Tp, w.nb, w.W, ncols, nc, ncols, w.W2, ncols, st)
+  e = (gemm_oz() && t_refl_tw) ? tw_par(t_refl_tw == 2, trans_t, Tp, w.nb, w.W, ncols, nc, ncols, w.W2, ncols, st)
                 : dgemm(trans_t, false, nc, ncols, nc, 1.0, Tp, w.nb, w.W, ncols, 0.0, w.W2, ncols, nullptr,
                         nullptr, st);
   if (e != cudaSuccess) return e;

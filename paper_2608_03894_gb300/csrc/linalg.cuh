@@ -43,7 +43,8 @@ void set_qr_panel_df(bool on);
 // For the calling thread in digit-slice mode, the two small products of each
 // block reflector: gram = 0 the Gram matrix V^T V as a digit-slice GEMM, 1 by
 // a parallel FP64 kernel, 2 by a parallel double-float kernel; tw = 0 op(T) W
-// as a digit-slice GEMM, 1 by a column-scaled double-float kernel.
+// as a digit-slice GEMM, 1 by a parallel FP64 kernel, 2 by a column-scaled
+// double-float kernel.
 void set_reflector_modes(int gram, int tw);
 bool gemm_oz();
 // While set_gemm_oz_tc(true) is in effect for the calling thread, the
