@@ -338,6 +338,60 @@ def stab_microbench(L):
         return {"L": L, "M": L, "sweep_s": round(time.time() - t, 3), "max_drift": d.stats()["max_drift"]}
 
 
+def batch_microbench(steps=2, warmup=1):
+    """The batched-chain workload: 64 independent chains on one GPU, 32 at
+    L = 12 (beta = 12, M = 120) and 32 at L = 16 (beta = 16, M = 160), U
+    cycling through -3, -4, -5, -6, mu = -1, dtau = 0.1, mixed precision,
+    every chain on its own stream and host thread (dqmc_batch_sweep). The
+    delay rank of each size is picked first by the autotuner (k in 16, 32,
+    64; n_stab 8; one timed sweep each at U = -4, drift bar 1e-6). One step
+    = one sweep of every chain; site-updates/s over the whole batch, device
+    time between two full synchronisations (CUDA events)."""
+    import torch
+
+    import paper_2608_03894_gb300 as pkg
+    sizes = ((12, 12.0), (16, 16.0))
+    tuned = {}
+    for L, beta in sizes:
+        r = pkg.autotune(L, beta, 0.1, -4.0, -1.0, seed=1, precision="mixed", ks=(16, 32, 64), n_stabs=(8,),
+                         warmup=1, sweeps=1, drift_bar=1e-6)
+        tuned[L] = {"k": r["k"], "n_stab": r["n_stab"], "sec_per_sweep": round(r["sec_per_sweep"], 4),
+                    "table": {f"k={k},n_stab={n}": (None if t is None else round(t, 4))
+                              for (k, n), t in r["table"].items()}}
+    params = []
+    for L, beta in sizes:
+        for i in range(32):
+            params.append((L, beta, 0.1, -(3.0 + i % 4), -1.0, len(params) + 1))
+    units = sum(2 * 3 * L * L * int(round(beta / 0.1)) for L, beta, *_ in params)
+    with pkg.Batch(params, precision="mixed") as b:
+        for c, p in zip(b.chains, params):
+            c.set_option("k", tuned[p[0]]["k"])
+            c.set_option("n_stab", tuned[p[0]]["n_stab"])
+        b.sweep(warmup)
+        sampler = ClockSampler(0)
+        torch.cuda.synchronize()
+        with sampler:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t0 = time.perf_counter()
+            b.sweep(steps)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = [c.stats() for c in b.chains]
+    return {"workload": "batch64: 32 chains at L=12 (N=432, beta=12, M=120) + 32 at L=16 (N=768, beta=16, "
+                        "M=160), U in {-3,-4,-5,-6}, mu=-1, dtau=0.1, mixed precision, autotuned k, "
+                        "one stream and host thread per chain",
+            "value": units * steps / (ms / 1000.0), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "wall_s_per_step": wall / steps,
+            "chain_sweeps_per_s": len(params) * steps / (ms / 1000.0), "site_updates_per_step": units,
+            "autotune": tuned, "max_drift": max(s["max_drift"] for s in stats),
+            "acceptance": sum(s["accepted"] for s in stats) / max(1, sum(s["proposed"] for s in stats)),
+            "clocks": sampler.summary()}
+
+
 def run_micro(args):
     import torch
     torch.cuda.set_device(0)
@@ -345,6 +399,9 @@ def run_micro(args):
     out = []
     if args.micro == "update":
         print(json.dumps({"micro": "update", "results": [update_microbench(args.micro_L)]}), flush=True)
+        return
+    if args.micro == "batch":
+        print(json.dumps({"micro": "batch", "results": [batch_microbench()]}), flush=True)
         return
     if args.micro == "stab":
         print(json.dumps({"micro": "stab", "results": [stab_microbench(args.micro_L)]}), flush=True)
@@ -639,12 +696,13 @@ def main():
                     help="sweeps timed for the plain FP64 (and FP32) comparator arms of a mixed "
                          "run; 0 skips them")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--micro", default=None, choices=("prop", "gemm", "metro", "update", "stab"),
+    ap.add_argument("--micro", default=None, choices=("prop", "gemm", "metro", "update", "stab", "batch"),
                     help="only a microbenchmark: the FFT propagation on a stacked operand larger "
                          "than L2 (prop; --micro-prec fp32,df,fp64), the stabilisation GEMM "
                          "(gemm; --micro-prec f64,df,oz,tc, size --micro-n), one delayed-update "
                          "block (metro; update: Metropolis + tensor-core flush, --micro-L), or a "
-                         "short chain whose refreshes run the stabilisation kernels (stab, --micro-L)")
+                         "short chain whose refreshes run the stabilisation kernels (stab, --micro-L), "
+                         "or the 64-chain batched workload with autotuned delay ranks (batch)")
     ap.add_argument("--micro-n", type=int, default=1728)
     ap.add_argument("--micro-L", type=int, default=24)
     ap.add_argument("--micro-stack", type=int, default=64)

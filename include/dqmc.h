@@ -162,10 +162,11 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                the GPU idle: 0 = digit slices, 1 = a parallel FP64 kernel
  *                (default), 2 = a parallel double-float kernel (its error costs
  *                the reflectors' orthogonality: L = 36 drift above 1e-6);
- *   "refl_tw"    with stab_gemm = 2: op(T) W of each block reflector as a
- *                column-scaled double-float kernel (1) instead of digit slices
- *                (0, default; 1 is ~3% faster per L = 24 sweep but drifts to
- *                ~1e-6 at L = 24 and 1.9e-6 at L = 36 over a few sweeps);
+ *   "refl_tw"    with stab_gemm = 2: op(T) W of each block reflector:
+ *                0 = digit slices, 1 = a parallel FP64 kernel (default;
+ *                ~3% faster per L = 24 sweep than 0), 2 = a column-scaled
+ *                double-float kernel (as fast as 1, but it drifts to ~1e-6
+ *                at L = 24 and 1.9e-6 at L = 36 over a few sweeps);
  *   "stab_gemm"  stabilisation GEMMs: 0 = FP64, 1 = double-float, 2 = exact
  *                7-bit digit slices on the bf16 tensor cores (default 2);
  *   "tc_gemm"    with stab_gemm = 2: 1 (default) = the digit-slice products
@@ -275,6 +276,27 @@ dqmc_status dqmc_load(dqmc_ctx *ctx, const char *path);
  * status. */
 dqmc_status dqmc_batch_create(int n, const double *params, dqmc_ctx **out);
 dqmc_status dqmc_batch_sweep(dqmc_ctx **ctxs, int n, int n_sweeps, int measure);
+
+/* Autotuner of the delay rank k and the refresh interval n_stab (the paper
+ * fixes both by hand, Sec. II): for every candidate pair (ks[a], n_stabs[b])
+ * a fresh chain of the given parameters, seed and precision (0 FP64, 1 mixed,
+ * 2 FP32) runs `warmup` untimed sweeps, then `sweeps` sweeps timed with CUDA
+ * events on a stream of its own; a pair whose max |G_wrapped - G_fresh| over
+ * those sweeps exceeds drift_bar is not admissible. On success *k_best and
+ * *n_stab_best get the admissible pair with the least time per sweep (the
+ * first in candidate order on ties) and *sec_per_sweep its time; times (NULL
+ * or nk * ns doubles, row a, column b) gets every pair's seconds per sweep,
+ * -1 for a pair that is not admissible. The FFT tiling is not a knob: the
+ * propagation kernel is specialised per L. Host pointers; the chains are
+ * created and destroyed inside the call (device memory from cudaMalloc).
+ * DQMC_EINVAL on empty candidate lists, a candidate < 1, warmup < 0,
+ * sweeps < 1, drift_bar <= 0, a precision other than 0, 1, 2, NULL outputs,
+ * a candidate the chain rejects, or when no pair is admissible; a failing
+ * chain's status otherwise. */
+dqmc_status dqmc_autotune(int L, double beta, double dtau, double U, double mu, uint64_t seed,
+                          int precision, const int *ks, int nk, const int *n_stabs, int ns,
+                          int warmup, int sweeps, double drift_bar, int *k_best, int *n_stab_best,
+                          double *sec_per_sweep, double *times);
 
 /* Message of the last failure on the calling host thread ("" if none); valid
  * until the thread's next failing call. */

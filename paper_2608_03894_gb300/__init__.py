@@ -10,7 +10,7 @@ from ._lib import DQMCError, LIB_PATH, load  # noqa: F401
 
 load()
 
-from .dqmc import DQMC, OBS_NAMES, Batch  # noqa: E402,F401
+from .dqmc import DQMC, OBS_NAMES, Batch, autotune  # noqa: E402,F401
 from . import ops  # noqa: E402,F401
 
-__all__ = ["DQMC", "Batch", "DQMCError", "OBS_NAMES", "ops", "load", "LIB_PATH"]
+__all__ = ["DQMC", "Batch", "autotune", "DQMCError", "OBS_NAMES", "ops", "load", "LIB_PATH"]

@@ -61,6 +61,8 @@ SIGNATURES = {
     "dqmc_destroy": (None, [vp]),
     "dqmc_batch_create": (i32, [i32, vp, vp]),
     "dqmc_batch_sweep": (i32, [vp, i32, i32, i32]),
+    "dqmc_autotune": (i32, [i32, f64, f64, f64, f64, u64, i32, vp, i32, vp, i32, i32, i32, f64,
+                            C.POINTER(i32), C.POINTER(i32), C.POINTER(f64), vp]),
     "dqmc_op_propagate_f64": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_propagate_f32": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),
     "dqmc_op_propagate_df": (i32, [i32, f64, i32, vp, vp, i32, i32, vp, vp, vp, vp]),

@@ -201,3 +201,24 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def autotune(L, beta, dtau, U, mu, seed=1, precision="mixed", ks=(16, 32, 64), n_stabs=(8,),
+             warmup=1, sweeps=1, drift_bar=1e-6):
+    """Delay rank and refresh interval by measurement (dqmc_autotune): every
+    (k, n_stab) pair timed on a fresh chain; returns the fastest pair whose
+    drift stays within drift_bar, its seconds per sweep, and the table of all
+    pairs (None for a pair over the bar)."""
+    lib = _lib.load()
+    prec = {"fp64": 0, "mixed": 1, "fp32": 2, 0: 0, 1: 1, 2: 2}[precision]
+    ka = (C.c_int * len(ks))(*[int(k) for k in ks])
+    na = (C.c_int * len(n_stabs))(*[int(n) for n in n_stabs])
+    times = (C.c_double * (len(ks) * len(n_stabs)))()
+    kb, nb, sec = C.c_int(0), C.c_int(0), C.c_double(0.0)
+    check(lib.dqmc_autotune(int(L), float(beta), float(dtau), float(U), float(mu),
+                            int(seed) & 0xFFFFFFFFFFFFFFFF, prec, ka, len(ks), na, len(n_stabs),
+                            int(warmup), int(sweeps), float(drift_bar), C.byref(kb), C.byref(nb),
+                            C.byref(sec), times))
+    table = {(int(k), int(n)): (times[a * len(n_stabs) + b] if times[a * len(n_stabs) + b] >= 0 else None)
+             for a, k in enumerate(ks) for b, n in enumerate(n_stabs)}
+    return {"k": kb.value, "n_stab": nb.value, "sec_per_sweep": sec.value, "table": table}

@@ -83,7 +83,8 @@ def test_create_and_destroy_without_gpu_work(lib):
     assert lib.dqmc_set_option(h, b"flush_tc", 0.0) == 0
     assert lib.dqmc_set_option(h, b"refl_gram", 2.0) == 0
     assert lib.dqmc_set_option(h, b"refl_gram", 3.0) == 1
-    assert lib.dqmc_set_option(h, b"refl_tw", 1.0) == 0
+    assert lib.dqmc_set_option(h, b"refl_tw", 2.0) == 0
+    assert lib.dqmc_set_option(h, b"refl_tw", 3.0) == 1
     assert lib.dqmc_set_option(h, b"df_panel", 1.0) == 0
     assert lib.dqmc_set_option(h, b"metro_reserve", 224 * 1024 + 1.0) == 1
     lib.dqmc_destroy(h)
@@ -142,6 +143,29 @@ def test_batch_create_validation(lib):
     assert lib.dqmc_batch_sweep(None, 1, 1, 0) == 1
     dup = (C.c_void_p * 2)(C.c_void_p(16), C.c_void_p(16))
     assert lib.dqmc_batch_sweep(dup, 2, 1, 0) == 1          # the same context twice
+
+
+def test_autotune_validation(lib):
+    """Argument checks of the autotuner, all before any chain is made."""
+    ks = (C.c_int * 2)(16, 32)
+    ns = (C.c_int * 1)(8)
+    kb, nb, sec = C.c_int(0), C.c_int(0), C.c_double(0.0)
+    outs = (C.byref(kb), C.byref(nb), C.byref(sec), None)
+
+    def call(ks_=ks, nk=2, ns_=ns, nn=1, prec=1, warmup=1, sweeps=1, bar=1e-6, o=outs):
+        return lib.dqmc_autotune(4, 2.0, 0.1, -4.0, -1.0, 1, prec, ks_, nk, ns_, nn, warmup, sweeps, bar, *o)
+
+    assert call(ks_=None) == 1
+    assert call(nk=0) == 1
+    assert call(nn=0) == 1
+    assert call(prec=3) == 1
+    assert call(warmup=-1) == 1
+    assert call(sweeps=0) == 1
+    assert call(bar=0.0) == 1
+    assert call(ks_=(C.c_int * 2)(16, 0)) == 1
+    assert call(ns_=(C.c_int * 1)(0)) == 1
+    assert call(o=(None, C.byref(nb), C.byref(sec), None)) == 1
+    assert b"autotune" in lib.dqmc_last_error()
 
 
 def _checkpoint(M=20, N=48, k=8, n_stab=10, prec=0, chain=0, bin_=10, st=(2, 1920, 900), md=1e-9,

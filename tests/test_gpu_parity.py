@@ -271,6 +271,34 @@ def test_green_from_scratch_fixed_field_L12(pkg):
             assert np.max(np.abs(d.green(l) - ogreen.green_udv(m, f, l))) < 1e-10
 
 
+def test_block_reflector_product_options_match_the_oracle(pkg):
+    """Mixed precision, L = 12, a forced-flip replay through three refreshes:
+    every kernel choice for the two small products of each block reflector of
+    the QR (the Gram matrix V^T V and op(T) W; 0 digit slices, 1 FP64, 2
+    double-float) gives the running G of the oracle's replay, to 1e-9 with
+    digit slices or FP64 and 1e-6 in double-float; the choices are live (their
+    results are not all bit-identical)."""
+    par = dict(L=12, beta=12.0, dtau=0.1, U=-4.0, mu=-1.0)
+    m = omodel.Model(**par)
+    f0 = random_field(m.M, m.N, seed=1)
+    flip = np.random.default_rng(2).random((m.M, m.N)) < 0.1
+    f1 = np.where(flip, -f0, f0).astype(np.int8)
+    sl = 33
+    ref = _oracle_replay(par, 10, f0, f1, sl)
+    out = {}
+    for gram, tw, tol in ((0, 0, 1e-9), (1, 0, 1e-9), (0, 1, 1e-9), (1, 1, 1e-9), (2, 2, 1e-6)):
+        with pkg.DQMC(**par, seed=1, k=32, n_stab=10, precision="mixed") as d:
+            d.set_option("refl_gram", gram)
+            d.set_option("refl_tw", tw)
+            d.field = f0
+            G = d.replay(f1, sl)
+        err = float(np.max(np.abs(G - ref.G)))
+        print(f"refl_gram={gram} refl_tw={tw}: |G - G_oracle| {err:.2e}")
+        assert err < tol
+        out[(gram, tw)] = G
+    assert not all(np.array_equal(out[(0, 0)], G) for G in out.values())
+
+
 def test_u0_closed_form_on_gpu(pkg):
     par = dict(L=12, beta=12.0, dtau=0.1, U=0.0, mu=-1.0)
     m = omodel.Model(**par)
@@ -426,6 +454,21 @@ def test_batched_chains_equal_single_chains(pkg):
             d.sweep(3, measure=True)
             assert np.array_equal(d.field, fields[i])
             assert d.measure()["n_samples"] == nsamp[i]
+
+
+def test_autotuner_picks_the_fastest_admissible_pair(pkg):
+    """dqmc_autotune at L = 4 (mixed): every candidate (k, n_stab) is timed,
+    the returned pair is the fastest one within the drift bar, and a bar that
+    no chain meets is reported as an error."""
+    ks, ns = (4, 8, 16), (5, 10)
+    r = pkg.autotune(4, 2.0, 0.1, -4.0, -1.0, seed=1, precision="mixed", ks=ks, n_stabs=ns,
+                     warmup=1, sweeps=1, drift_bar=1e-6)
+    assert set(r["table"]) == {(k, n) for k in ks for n in ns}
+    adm = {p: t for p, t in r["table"].items() if t is not None}
+    assert adm and all(t > 0 for t in adm.values())
+    assert r["table"][(r["k"], r["n_stab"])] == min(adm.values()) == r["sec_per_sweep"]
+    with pytest.raises(pkg.DQMCError):
+        pkg.autotune(4, 2.0, 0.1, -4.0, -1.0, ks=(8,), n_stabs=(10,), drift_bar=1e-300)
 
 
 @pytest.mark.parametrize("L,beta,k,n_stab,prec", [
