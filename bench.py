@@ -343,30 +343,44 @@ def batch_microbench(steps=2, warmup=1):
     L = 12 (beta = 12, M = 120) and 32 at L = 16 (beta = 16, M = 160), U
     cycling through -3, -4, -5, -6, mu = -1, dtau = 0.1, mixed precision,
     every chain on its own stream and host thread (dqmc_batch_sweep). The
-    delay rank of each size is picked first by the autotuner (k in 16, 32,
-    64; n_stab 8; one timed sweep each at U = -4, drift bar 1e-6). One step
-    = one sweep of every chain; site-updates/s over the whole batch, device
-    time between two full synchronisations (CUDA events)."""
+    autotuner picks first the delay rank of each size (k in 16, 32, 64 at
+    U = -4, n_stab 8), then the refresh interval of each U at the larger size
+    (n_stab in 4, 6, 8, drift bar 3e-7 over its two sweeps: stronger coupling
+    amplifies the wrap error faster). One step = one sweep of every chain;
+    site-updates/s over the whole batch, device time between two full
+    synchronisations (CUDA events)."""
     import torch
 
     import paper_2608_03894_gb300 as pkg
     sizes = ((12, 12.0), (16, 16.0))
-    tuned = {}
+    Us = (-3.0, -4.0, -5.0, -6.0)
+
+    def table(r):
+        return {f"k={k},n_stab={n}": (None if t is None else round(t, 4)) for (k, n), t in r["table"].items()}
+
+    tuned_k, tuned_ns = {}, {}
     for L, beta in sizes:
         r = pkg.autotune(L, beta, 0.1, -4.0, -1.0, seed=1, precision="mixed", ks=(16, 32, 64), n_stabs=(8,),
                          warmup=1, sweeps=1, drift_bar=1e-6)
-        tuned[L] = {"k": r["k"], "n_stab": r["n_stab"], "sec_per_sweep": round(r["sec_per_sweep"], 4),
-                    "table": {f"k={k},n_stab={n}": (None if t is None else round(t, 4))
-                              for (k, n), t in r["table"].items()}}
+        tuned_k[L] = {"k": r["k"], "sec_per_sweep": round(r["sec_per_sweep"], 4), "table": table(r)}
+    L, beta = sizes[-1]
+    for U in Us:
+        try:
+            r = pkg.autotune(L, beta, 0.1, U, -1.0, seed=1, precision="mixed", ks=(tuned_k[L]["k"],),
+                             n_stabs=(4, 6, 8), warmup=1, sweeps=1, drift_bar=3e-7)
+        except pkg.DQMCError:
+            r = pkg.autotune(L, beta, 0.1, U, -1.0, seed=1, precision="mixed", ks=(tuned_k[L]["k"],),
+                             n_stabs=(2,), warmup=1, sweeps=1, drift_bar=1e-6)
+        tuned_ns[U] = {"n_stab": r["n_stab"], "sec_per_sweep": round(r["sec_per_sweep"], 4), "table": table(r)}
     params = []
     for L, beta in sizes:
         for i in range(32):
-            params.append((L, beta, 0.1, -(3.0 + i % 4), -1.0, len(params) + 1))
+            params.append((L, beta, 0.1, Us[i % 4], -1.0, len(params) + 1))
     units = sum(2 * 3 * L * L * int(round(beta / 0.1)) for L, beta, *_ in params)
     with pkg.Batch(params, precision="mixed") as b:
         for c, p in zip(b.chains, params):
-            c.set_option("k", tuned[p[0]]["k"])
-            c.set_option("n_stab", tuned[p[0]]["n_stab"])
+            c.set_option("k", tuned_k[p[0]]["k"])
+            c.set_option("n_stab", tuned_ns[p[3]]["n_stab"])
         b.sweep(warmup)
         sampler = ClockSampler(0)
         torch.cuda.synchronize()
@@ -381,13 +395,17 @@ def batch_microbench(steps=2, warmup=1):
             torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         stats = [c.stats() for c in b.chains]
+    drift = {f"L={L},U={U}": max(s["max_drift"] for s, p in zip(stats, params) if p[0] == L and p[3] == U)
+             for L, _ in sizes for U in Us}
     return {"workload": "batch64: 32 chains at L=12 (N=432, beta=12, M=120) + 32 at L=16 (N=768, beta=16, "
-                        "M=160), U in {-3,-4,-5,-6}, mu=-1, dtau=0.1, mixed precision, autotuned k, "
-                        "one stream and host thread per chain",
+                        "M=160), U in {-3,-4,-5,-6}, mu=-1, dtau=0.1, mixed precision, autotuned k and "
+                        "n_stab, one stream and host thread per chain",
             "value": units * steps / (ms / 1000.0), "unit": UNIT, "steps": steps, "warmup": warmup,
             "ms_per_step": ms / steps, "wall_s_per_step": wall / steps,
             "chain_sweeps_per_s": len(params) * steps / (ms / 1000.0), "site_updates_per_step": units,
-            "autotune": tuned, "max_drift": max(s["max_drift"] for s in stats),
+            "autotune_k": {str(k): v for k, v in tuned_k.items()},
+            "autotune_n_stab": {str(u): v for u, v in tuned_ns.items()},
+            "max_drift": max(drift.values()), "max_drift_by_group": drift,
             "acceptance": sum(s["accepted"] for s in stats) / max(1, sum(s["proposed"] for s in stats)),
             "clocks": sampler.summary()}
 
@@ -702,7 +720,8 @@ def main():
                          "(gemm; --micro-prec f64,df,oz,tc, size --micro-n), one delayed-update "
                          "block (metro; update: Metropolis + tensor-core flush, --micro-L), or a "
                          "short chain whose refreshes run the stabilisation kernels (stab, --micro-L), "
-                         "or the 64-chain batched workload with autotuned delay ranks (batch)")
+                         "or the 64-chain batched workload with autotuned delay ranks and refresh "
+                         "intervals (batch)")
     ap.add_argument("--micro-n", type=int, default=1728)
     ap.add_argument("--micro-L", type=int, default=24)
     ap.add_argument("--micro-stack", type=int, default=64)
