@@ -118,10 +118,12 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  *                    "flush_tc"), else in double-float arithmetic (FP32
  *                    pairs, ~2^-47) on the FP32 units; FFT
  *                    propagation in FP64 (see "df_prop"); stabilisation
- *                    products as exact digit slices
- *                    on the bf16 tensor cores; Metropolis decisions and
- *                    Woodbury coefficients in double-float (see "df_metro");
- *                    Householder panels and triangular inverses in FP64;
+ *                    products as exact digit slices on the bf16 tensor
+ *                    cores, except the two small products of each block
+ *                    reflector (FP64 kernels, see "refl_gram", "refl_tw");
+ *                    Metropolis decisions and Woodbury coefficients in
+ *                    double-float (see "df_metro"); Householder panels and
+ *                    triangular inverses in FP64;
  *                2 = plain FP32 propagation and flush, which drifts by
  *                    1e-3..1e-1 per refresh interval (for comparison);
  *   "chain"      Philox chain id;
@@ -141,10 +143,12 @@ dqmc_status dqmc_create(int L, double beta, double dtau, double U, double mu, ui
  * mixed precision only (1 = double-float, 0 = native FP64 for that step):
  *   "df_flush"   rank-m flush as double-float products (default 1);
  *   "flush_tc"   with df_flush = 1 and k = 32: the flush as digit slices on
- *                tcgen05 (dqmc_op_flush_tc), the blocks one after another on
- *                the context's stream ("pipeline" does not apply) (default 1;
- *                0 = the double-float flush); a bounded wait of its kernel
- *                that gives up makes dqmc_sweep return DQMC_ETIMEOUT;
+ *                tcgen05 (dqmc_op_flush_tc), whose digit-tile kernel also
+ *                forms the next block's look-ahead rows; with "pipeline" = 1
+ *                the next block's Metropolis runs on the second stream beside
+ *                the flush (default 1; 0 = the double-float flush); a bounded
+ *                wait of its kernel that gives up makes dqmc_sweep return
+ *                DQMC_ETIMEOUT;
  *   "df_prop"    FFT propagation in double-float arithmetic (default 0: the
  *                propagation is ~4% of a sweep, and its rounding, applied to
  *                the whole G every slice, dominated the double-float drift at
